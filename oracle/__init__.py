@@ -1,0 +1,14 @@
+"""FP64 CPU oracle for the THIIM E/H sweeps.
+
+TEST INFRASTRUCTURE ONLY: imported by ``tests/``, ``__graft_entry__.smoke()``
+and the CPU-baseline leg of ``bench.py``.  The product package never imports,
+links or executes anything here, and nothing here imports the product.
+
+* ``thiim_oracle.c``  the 12 split updates as plain loop nests (Eqs. 3-7,
+  Listings 1-2), compiled by ``build.py`` with gcc.
+* ``coeffs.py``       the per-cell coefficient arrays t, c and the source
+  arrays derived from Eqs. 3-5, in NumPy FP64.
+* ``adjoint.py``      the transposed iteration and parameter gradients.
+"""
+from .thiim_oracle import iterate, rule, SPLITS, FIELD_INDEX, COEFF_NAMES  # noqa: F401
+from .coeffs import build_coeffs, incident_wave, discrete_omega  # noqa: F401

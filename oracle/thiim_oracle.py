@@ -1,0 +1,72 @@
+"""ctypes front end of the C oracle (test infrastructure only).
+
+Arrays are NumPy complex128, C-contiguous, shape (nz, ny, nx): the layout of
+the paper's listings (x fastest).  Updates happen in place.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import build as _build
+
+SPLITS = ["Hxy", "Hxz", "Hyx", "Hyz", "Hzx", "Hzy", "Exy", "Exz", "Eyx", "Eyz", "Ezx", "Ezy"]
+FIELD_INDEX = {n: i for i, n in enumerate(SPLITS)}
+COEFF_NAMES = (["t" + s for s in SPLITS] + ["c" + s for s in SPLITS]
+               + ["SrcHxy", "SrcHyx", "SrcExy", "SrcEyx"])
+
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        lib = ctypes.CDLL(_build.build())
+        pp = ctypes.POINTER(ctypes.c_void_p)
+        lib.oracle_iterate.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_uint,
+                                       pp, pp, ctypes.c_int, ctypes.c_int,
+                                       ctypes.POINTER(ctypes.c_double)]
+        lib.oracle_iterate.restype = ctypes.c_int
+        ip = ctypes.POINTER(ctypes.c_int)
+        lib.oracle_rule.argtypes = [ctypes.c_int, ip, ip, ip, ip, ip]
+        lib.oracle_rule.restype = ctypes.c_int
+        _lib = lib
+    return _lib
+
+
+def _ptrs(arrays, shape):
+    out = (ctypes.c_void_p * len(arrays))()
+    for n, a in enumerate(arrays):
+        if a.dtype != np.complex128 or not a.flags.c_contiguous or a.shape != shape:
+            raise ValueError("oracle arrays must be C-contiguous complex128 of shape %s" % (shape,))
+        out[n] = a.ctypes.data
+    return out
+
+
+def iterate(fields, coeffs, n: int, bc: int = 3, nthreads: int = 1) -> float:
+    """Run n THIIM iterations in place; return ||x^n - x^{n-1}|| / ||x^n|| (FP64).
+
+    bc: bit 0 periodic x, bit 1 periodic y, bit 2 periodic z (else zero outside).
+    """
+    lib = _load()
+    if len(fields) != 12 or len(coeffs) != 28:
+        raise ValueError("need 12 field and 28 coefficient arrays")
+    shape = fields[0].shape
+    nz, ny, nx = shape
+    fp = _ptrs(fields, shape)
+    cp = _ptrs(coeffs, shape)
+    rel = ctypes.c_double(0.0)
+    rc = lib.oracle_iterate(nx, ny, nz, bc, fp, cp, int(n), int(nthreads), ctypes.byref(rel))
+    if rc != 0:
+        raise ValueError("oracle_iterate rejected its arguments")
+    return rel.value
+
+
+def rule(s: int):
+    """(direction, src_a, src_b, sign, src_array) of split s: direction 0=x, 1=y, 2=z."""
+    lib = _load()
+    v = [ctypes.c_int() for _ in range(5)]
+    if lib.oracle_rule(s, *[ctypes.byref(x) for x in v]) != 0:
+        raise ValueError(s)
+    return tuple(x.value for x in v)
