@@ -1,0 +1,178 @@
+/*
+ * thiim.h — C ABI of the GB300 THIIM E/H sweep library (libthiim.so).
+ *
+ * The library runs the hot path of the Time Harmonic Inverse Iteration
+ * Method (Malas et al., "Optimization of an electromagnetics code with
+ * multicore wavefront diamond blocking and multi-dimensional intra-tile
+ * parallelization", arXiv 1510.05218): the coupled H-field and E-field update
+ * sweeps of Eqs. 3-5 over the staggered Yee grid with the split-field
+ * absorbing layer of Eqs. 6-7 (Sec. I-A), whose per-cell data are the 12
+ * split field arrays and 28 coefficient arrays of Sec. III.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Grid:    nx * ny * nz cells; cell (i, j, k) is element (k*ny + j)*nx + i
+ *          of every array (x fastest, the layout of Listing 1).
+ * Arrays:  contiguous complex values, interleaved (re, im):
+ *          THIIM_C128 -> 16-byte double complex, 16-byte aligned;
+ *          THIIM_C64  ->  8-byte float complex,   8-byte aligned.
+ * Fields:  12 splits, in this order (split F_ab of component a reads
+ *          component b of the other field, as in Listings 1-2):
+ *            Hxy Hxz Hyx Hyz Hzx Hzy Exy Exz Eyx Eyz Ezx Ezy
+ * Coeffs:  28 arrays: t[12] and c[12] in the field order, then the source
+ *          arrays SrcHxy SrcHyx SrcExy SrcEyx (Sec. III: 4*3 + 8*2 = 28).
+ * Update:  x_s <- t_s x_s + Src_s + sign_s c_s D_s(F)   (Listings 1-2)
+ *          where F is the full component that split s reads (sum of its two
+ *          splits), D is a backward difference for H (reads k-1, j-1, i-1)
+ *          and a forward difference for E (reads +1), and sign_s is the sign
+ *          of the term in the curl:
+ *            Hxy +dz Ey  Hxz -dy Ez  Hyx -dz Ex  Hyz +dx Ez  Hzx +dy Ex  Hzy -dx Ey
+ *            Exy -dz Hy  Exz +dy Hz  Eyx +dz Hx  Eyz -dx Hz  Ezx -dy Hx  Ezy +dx Hy
+ * Order:   one iteration = all six H updates (reading E^n), then all six E
+ *          updates (reading the new H), Eqs. 3-4.
+ * Bounds:  THIIM_PERIODIC_X/Y/Z wrap the index; a direction without its flag
+ *          reads zero outside the grid (homogeneous Dirichlet, Sec. II-B).
+ * Memory:  the caller owns every field, coefficient, lambda and gradient
+ *          buffer (device memory); the library borrows the pointers until the
+ *          next set call or thiim_destroy and owns only its context and
+ *          scratch (a second field set of 12 arrays for the out-of-place
+ *          sweep, and a few kilobytes of reduction partials).
+ * Streams: all work is enqueued on the stream given to thiim_create (a
+ *          cudaStream_t; NULL = legacy default stream) and returns before it
+ *          runs, except calls documented as synchronising.
+ * Errors:  every int-returning call returns THIIM_OK (0) or a negative
+ *          thiim_status; no exception or abort crosses the ABI.  A call that
+ *          fails leaves the context usable and the fields unchanged unless
+ *          stated otherwise.
+ */
+#ifndef THIIM_H
+#define THIIM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct thiim_ctx thiim_ctx;
+
+enum thiim_precision {
+    THIIM_C128 = 0, /* complex128 storage, FP64 arithmetic */
+    THIIM_C64 = 1   /* complex64 storage, FP32 arithmetic */
+};
+
+enum thiim_bc_flags {
+    THIIM_PERIODIC_X = 1u,
+    THIIM_PERIODIC_Y = 2u,
+    THIIM_PERIODIC_Z = 4u
+};
+
+enum thiim_status {
+    THIIM_OK = 0,
+    THIIM_ERR_ARG = -1,       /* bad size, count, flag or NULL pointer */
+    THIIM_ERR_ALIGN = -2,     /* an array is not aligned to its element size */
+    THIIM_ERR_STATE = -3,     /* call order violated (e.g. iterate before set_fields) */
+    THIIM_ERR_CUDA = -4,      /* a CUDA runtime call or kernel launch failed */
+    THIIM_ERR_TIMEOUT = -5,   /* a bounded device-side wait expired */
+    THIIM_ERR_NONFINITE = -6, /* a reduction saw NaN or Inf */
+    THIIM_ERR_NOMEM = -7      /* the library could not allocate its scratch */
+};
+
+/* Number of field / coefficient arrays (Sec. III). */
+#define THIIM_N_FIELDS 12
+#define THIIM_N_COEFFS 28
+
+/*
+ * thiim_create — make a context for an nx * ny * nz grid.
+ *   precision: enum thiim_precision.
+ *   bc_flags:  OR of enum thiim_bc_flags (the stack workloads use X|Y,
+ *              Dirichlet in z behind the absorbing layers, Sec. I-A).
+ *   cuda_stream: cudaStream_t on which every later call enqueues its work.
+ * *out receives the context.  Errors: THIIM_ERR_ARG for sizes < 1, a cell
+ * count above 2^40, an unknown precision or flag; THIIM_ERR_CUDA if the
+ * device cannot be queried.  Allocates only the context itself.
+ */
+int thiim_create(thiim_ctx **out, int nx, int ny, int nz, int precision,
+                 unsigned bc_flags, void *cuda_stream);
+
+/* Replace the stream used by later calls. */
+int thiim_set_stream(thiim_ctx *ctx, void *cuda_stream);
+
+/*
+ * thiim_set_coeffs — borrow the 28 coefficient arrays (device pointers, in the
+ * context's precision, layout above).  Errors: THIIM_ERR_ARG on NULL,
+ * THIIM_ERR_ALIGN on misalignment.
+ */
+int thiim_set_coeffs(thiim_ctx *ctx, void *const coeff[THIIM_N_COEFFS]);
+
+/*
+ * thiim_set_fields — borrow the 12 field arrays (device pointers).  They hold
+ * the current iterate x^n and are updated in place by thiim_iterate.  The
+ * first call allocates the library's second field set (12 arrays of the same
+ * size) used by the out-of-place sweep; THIIM_ERR_NOMEM if that fails.
+ */
+int thiim_set_fields(thiim_ctx *ctx, void *const field[THIIM_N_FIELDS]);
+
+/*
+ * thiim_iterate — enqueue n_iters THIIM iterations (Eqs. 3-5): each is the
+ * six H half-step updates followed by the six E updates.  When it completes
+ * on the stream, the caller's field arrays hold x^{n + n_iters}.  The last
+ * iteration also accumulates, in FP64, the norms that thiim_residual reports.
+ * n_iters = 0 does nothing.  Errors: THIIM_ERR_STATE if fields or
+ * coefficients are missing, THIIM_ERR_ARG if n_iters < 0, THIIM_ERR_CUDA.
+ */
+int thiim_iterate(thiim_ctx *ctx, int n_iters);
+
+/*
+ * thiim_residual — synchronises the stream and returns in *rel_residual the
+ * relative update of the most recent iteration run by thiim_iterate,
+ *   || F^{n} - F^{n-1} ||_2 / || F^{n} ||_2,
+ * over the six full field components F (Ex = Exy + Exz, ..., Hz = Hzx + Hzy)
+ * of every cell, accumulated in FP64.  (The split parts alone do not settle
+ * where sigma* = 0: their difference is not driven, so the full fields are
+ * the converging quantity.)  Returns 0 in *rel_residual when F^n = 0.
+ * Errors: THIIM_ERR_STATE if no iteration ran since set_fields,
+ * THIIM_ERR_NONFINITE if a norm is NaN or Inf, THIIM_ERR_CUDA.
+ */
+int thiim_residual(thiim_ctx *ctx, double *rel_residual);
+
+/*
+ * thiim_build_coeffs — fill the 28 coefficient arrays of a layered problem
+ * from per-cell material data, in the context's precision (the discrete
+ * Eqs. 3-5 solved for the new value; Eq. 5 where Re(eps_r) < 0):
+ *   eps_r:       device array of nx*ny*nz complex128 relative permittivities
+ *                in the physics convention (Im > 0 lossy); the paper's fields
+ *                vary as e^{+i omega t}, so the material conductivity is
+ *                sigma = omega * Im(eps_r) and eps = Re(eps_r).  mu = 1.
+ *   sigma_pml_e: host array of nz absorbing-layer conductivities at the E
+ *                planes (z = k); added to the four splits that difference
+ *                along z (Hxy, Hyx, Exy, Eyx) — for H from sigma_pml_h
+ *                (H plane k sits at z = k - 1/2).  NULL = none.
+ *   omega, tau:  frequency and pseudo time step (tau > 0).
+ *   k_s, amp:    plane-wave source: an x-polarised wave of complex amplitude
+ *                (amp_re, amp_im) enters at the total-field/scattered-field
+ *                plane k_s (E planes >= k_s and H planes > k_s are total
+ *                field); k_s < 0 means no source (all Src arrays zero).
+ *   coeff:       28 device arrays (may equal those given to set_coeffs).
+ * Errors: THIIM_ERR_ARG (NULL, tau <= 0, k_s >= nz, omega tau beyond the
+ * discrete dispersion range), THIIM_ERR_ALIGN, THIIM_ERR_CUDA.
+ */
+int thiim_build_coeffs(thiim_ctx *ctx, const void *eps_r,
+                       const double *sigma_pml_e, const double *sigma_pml_h,
+                       double omega, double tau, int k_s, double amp_re,
+                       double amp_im, void *const coeff[THIIM_N_COEFFS]);
+
+/* Release the context and its scratch (synchronises the stream first). */
+void thiim_destroy(thiim_ctx *ctx);
+
+/* Static, human-readable text of a thiim_status code. */
+const char *thiim_strerror(int status);
+
+/* Library version as major*10000 + minor*100 + patch. */
+int thiim_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* THIIM_H */

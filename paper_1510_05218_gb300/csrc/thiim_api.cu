@@ -1,0 +1,391 @@
+// C ABI of the THIIM sweep library: context, argument checks, launches,
+// the residual reduction and the coefficient builder.  See include/thiim.h.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+
+#include "../../include/thiim.h"
+#include "thiim_internal.h"
+
+using namespace thiim;
+
+struct thiim_ctx {
+    int nx, ny, nz;
+    int precision;
+    unsigned bc;
+    cudaStream_t stream;
+    int device;
+    int num_sms;
+    size_t elem;                 // bytes per complex element
+    size_t n_cells;
+    void *coeff[THIIM_N_COEFFS];
+    void *user[THIIM_N_FIELDS];  // caller's field arrays (hold x^n between calls)
+    void *alt[THIIM_N_FIELDS];   // library's second field set
+    bool have_coeffs, have_fields, have_norm;
+    int zchunk;                  // planes per CTA of the sweep
+    double *partials;            // 2 doubles per sweep CTA
+    size_t partials_cap;         // in CTAs
+    double *norms;               // device: |dF|^2, |F|^2 of the last iteration
+    double *pml;                 // device: 2*nz absorbing-layer conductivities
+    int *flag;                   // device: error flag of the coefficient builder
+};
+
+namespace {
+
+int cuda_status(cudaError_t e) { return e == cudaSuccess ? THIIM_OK : THIIM_ERR_CUDA; }
+
+bool aligned(const void *p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+int tiles_x(const thiim_ctx *c) { return (c->nx + SWEEP_TX - 1) / SWEEP_TX; }
+int tiles_y(const thiim_ctx *c) { return (c->ny + SWEEP_TY - 1) / SWEEP_TY; }
+
+// Planes per CTA: enough CTAs along z that the grid covers every SM several
+// times, but at least 8 planes so the one-plane prologue and lookahead of a
+// chunk stay cheap.
+int default_zchunk(const thiim_ctx *c) {
+    const long tiles = (long)tiles_x(c) * tiles_y(c);
+    const long target = 8L * c->num_sms;
+    long chunks = (target + tiles - 1) / tiles;
+    long maxchunks = c->nz / 8 > 0 ? c->nz / 8 : 1;
+    if (chunks > maxchunks) chunks = maxchunks;
+    if (chunks < 1) chunks = 1;
+    return (int)((c->nz + chunks - 1) / chunks);
+}
+
+int ensure_partials(thiim_ctx *c, size_t ctas) {
+    if (c->partials_cap >= ctas) return THIIM_OK;
+    if (c->partials) cudaFree(c->partials);
+    c->partials = nullptr;
+    c->partials_cap = 0;
+    if (cudaMalloc(&c->partials, 2 * ctas * sizeof(double)) != cudaSuccess) return THIIM_ERR_NOMEM;
+    c->partials_cap = ctas;
+    return THIIM_OK;
+}
+
+// Sum the per-CTA partial pairs in a fixed order (deterministic).
+__global__ void finalize_norms(const double *partials, size_t n, double *out) {
+    __shared__ double sd[256], sx[256];
+    double d = 0.0, x = 0.0;
+    for (size_t i = threadIdx.x; i < n; i += blockDim.x) {
+        d += partials[2 * i];
+        x += partials[2 * i + 1];
+    }
+    sd[threadIdx.x] = d;
+    sx[threadIdx.x] = x;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) {
+            sd[threadIdx.x] += sd[threadIdx.x + o];
+            sx[threadIdx.x] += sx[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) { out[0] = sd[0]; out[1] = sx[0]; }
+}
+
+// ---- coefficient builder (Eqs. 3-5 solved for the new value) ---------------
+
+struct dc { double x, y; };
+__device__ __forceinline__ dc mk(double x, double y) { dc r; r.x = x; r.y = y; return r; }
+__device__ __forceinline__ dc cmul(dc a, dc b) { return mk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+__device__ __forceinline__ dc cdiv(dc a, dc b) {
+    const double den = b.x * b.x + b.y * b.y;
+    return mk((a.x * b.x + a.y * b.y) / den, (a.y * b.x - a.x * b.y) / den);
+}
+__device__ __forceinline__ dc cexpi(double t) { double s, c; sincos(t, &s, &c); return mk(c, s); }
+
+struct BuildArgs {
+    const double2 *eps;
+    const double *sig_e;      // nz
+    const double *sig_h;      // nz
+    void *co[THIIM_N_COEFFS];
+    int nx, ny, nz;
+    double omega, tau;
+    int k_s;                  // -1: no source
+    dc src_h;                 // factor of c_Hyx at k_s
+    dc src_e;                 // factor of c_Exy at k_s
+    int *flag;
+};
+
+// Splits that difference along z carry the absorbing-layer conductivity.
+__device__ __forceinline__ bool along_z(int s) { return s == HXY || s == HYX || s == EXY || s == EYX; }
+
+template <typename V>
+__device__ __forceinline__ void put(void *base, size_t i, dc v) {
+    V w;
+    w.x = (decltype(w.x))v.x;
+    w.y = (decltype(w.y))v.y;
+    reinterpret_cast<V *>(base)[i] = w;
+}
+
+template <typename V>
+__global__ void build_coeffs_kernel(const BuildArgs a) {
+    const size_t n = (size_t)a.nx * a.ny * a.nz;
+    const size_t plane = (size_t)a.nx * a.ny;
+    const double wt = a.omega * a.tau;
+    const dc e_mh = cexpi(-0.5 * wt), e_ph = cexpi(0.5 * wt);
+    const dc e_m1 = cexpi(-wt), e_p1 = cexpi(wt);
+    for (size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (size_t)gridDim.x * blockDim.x) {
+        const int k = (int)(p / plane);
+        const double2 er = a.eps[p];
+        const double eps = er.x;
+        const double sig_mat = a.omega * er.y;
+        if (!(eps != 0.0) || !isfinite(eps) || !isfinite(er.y)) atomicOr(a.flag, 1);
+        dc c_hyx = mk(0, 0), c_exy = mk(0, 0);
+        for (int s = 0; s < 12; ++s) {
+            dc t, c;
+            if (s < 6) {             // H, Eq. 4 (mu = 1)
+                const double ss = along_z(s) ? a.sig_h[k] : 0.0;
+                const dc den = mk(e_ph.x + a.tau * ss, e_ph.y);
+                t = cdiv(e_mh, den);
+                c = cdiv(mk(a.tau, 0.0), den);
+            } else {
+                const double sg = sig_mat + (along_z(s) ? a.sig_e[k] : 0.0);
+                if (eps > 0.0) {     // Eq. 3
+                    t = cdiv(e_m1, mk(1.0 + a.tau * sg / eps, 0.0));
+                    c = cdiv(mk(a.tau * e_mh.x, a.tau * e_mh.y), mk(eps + a.tau * sg, 0.0));
+                } else {             // Eq. 5, back iteration
+                    t = cdiv(e_p1, mk(1.0 - a.tau * sg / eps, 0.0));
+                    c = cdiv(mk(-a.tau * e_ph.x, -a.tau * e_ph.y), mk(eps - a.tau * sg, 0.0));
+                }
+            }
+            put<V>(a.co[T0 + s], p, t);
+            put<V>(a.co[C0 + s], p, c);
+            if (s == HYX) c_hyx = c;
+            if (s == EXY) c_exy = c;
+        }
+        dc s_hyx = mk(0, 0), s_exy = mk(0, 0);
+        if (k == a.k_s) {
+            s_hyx = cmul(c_hyx, a.src_h);
+            s_exy = cmul(c_exy, a.src_e);
+        }
+        put<V>(a.co[SRC_HXY], p, mk(0, 0));
+        put<V>(a.co[SRC_HYX], p, s_hyx);
+        put<V>(a.co[SRC_EXY], p, s_exy);
+        put<V>(a.co[SRC_EYX], p, mk(0, 0));
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+int thiim_version(void) { return 1 * 10000 + 0 * 100 + 0; }
+
+const char *thiim_strerror(int status) {
+    switch (status) {
+        case THIIM_OK: return "ok";
+        case THIIM_ERR_ARG: return "invalid argument";
+        case THIIM_ERR_ALIGN: return "misaligned array";
+        case THIIM_ERR_STATE: return "call order violated (fields or coefficients not set, or no iteration yet)";
+        case THIIM_ERR_CUDA: return "CUDA runtime error";
+        case THIIM_ERR_TIMEOUT: return "bounded device wait expired";
+        case THIIM_ERR_NONFINITE: return "non-finite value in a reduction";
+        case THIIM_ERR_NOMEM: return "device allocation failed";
+        default: return "unknown status";
+    }
+}
+
+int thiim_create(thiim_ctx **out, int nx, int ny, int nz, int precision, unsigned bc_flags,
+                 void *cuda_stream) {
+    if (!out) return THIIM_ERR_ARG;
+    *out = nullptr;
+    if (nx < 1 || ny < 1 || nz < 1) return THIIM_ERR_ARG;
+    if ((double)nx * ny * nz > (double)(1ull << 40)) return THIIM_ERR_ARG;
+    if (precision != THIIM_C128 && precision != THIIM_C64) return THIIM_ERR_ARG;
+    if (bc_flags & ~7u) return THIIM_ERR_ARG;
+    thiim_ctx *c = new (std::nothrow) thiim_ctx();
+    if (!c) return THIIM_ERR_NOMEM;
+    c->nx = nx; c->ny = ny; c->nz = nz;
+    c->precision = precision;
+    c->bc = bc_flags;
+    c->stream = (cudaStream_t)cuda_stream;
+    c->elem = precision == THIIM_C128 ? 16 : 8;
+    c->n_cells = (size_t)nx * ny * nz;
+    if (cudaGetDevice(&c->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) {
+        delete c;
+        return THIIM_ERR_CUDA;
+    }
+    c->zchunk = default_zchunk(c);
+    *out = c;
+    return THIIM_OK;
+}
+
+int thiim_set_stream(thiim_ctx *c, void *cuda_stream) {
+    if (!c) return THIIM_ERR_ARG;
+    c->stream = (cudaStream_t)cuda_stream;
+    return THIIM_OK;
+}
+
+int thiim_set_coeffs(thiim_ctx *c, void *const coeff[THIIM_N_COEFFS]) {
+    if (!c || !coeff) return THIIM_ERR_ARG;
+    for (int i = 0; i < THIIM_N_COEFFS; ++i) {
+        if (!coeff[i]) return THIIM_ERR_ARG;
+        if (!aligned(coeff[i], c->elem)) return THIIM_ERR_ALIGN;
+    }
+    memcpy(c->coeff, coeff, sizeof(c->coeff));
+    c->have_coeffs = true;
+    return THIIM_OK;
+}
+
+int thiim_set_fields(thiim_ctx *c, void *const field[THIIM_N_FIELDS]) {
+    if (!c || !field) return THIIM_ERR_ARG;
+    for (int i = 0; i < THIIM_N_FIELDS; ++i) {
+        if (!field[i]) return THIIM_ERR_ARG;
+        if (!aligned(field[i], c->elem)) return THIIM_ERR_ALIGN;
+    }
+    if (!c->alt[0]) {
+        for (int i = 0; i < THIIM_N_FIELDS; ++i) {
+            if (cudaMalloc(&c->alt[i], c->n_cells * c->elem) != cudaSuccess) {
+                for (int j = 0; j < i; ++j) { cudaFree(c->alt[j]); c->alt[j] = nullptr; }
+                c->alt[i] = nullptr;
+                cudaGetLastError();
+                return THIIM_ERR_NOMEM;
+            }
+        }
+    }
+    memcpy(c->user, field, sizeof(c->user));
+    c->have_fields = true;
+    c->have_norm = false;
+    return THIIM_OK;
+}
+
+int thiim_iterate(thiim_ctx *c, int n_iters) {
+    if (!c || n_iters < 0) return THIIM_ERR_ARG;
+    if (!c->have_fields || !c->have_coeffs) return THIIM_ERR_STATE;
+    if (n_iters == 0) return THIIM_OK;
+    const int tx = tiles_x(c), ty = tiles_y(c);
+    const int chunks = (c->nz + c->zchunk - 1) / c->zchunk;
+    const dim3 grid((unsigned)(tx * ty), (unsigned)chunks);
+    const size_t ctas = (size_t)tx * ty * chunks;
+    int st = ensure_partials(c, ctas);
+    if (st) return st;
+    if (!c->norms && cudaMalloc(&c->norms, 2 * sizeof(double)) != cudaSuccess) return THIIM_ERR_NOMEM;
+
+    SweepArgs a;
+    memset(&a, 0, sizeof(a));
+    memcpy(a.co, c->coeff, sizeof(a.co));
+    a.nx = c->nx; a.ny = c->ny; a.nz = c->nz;
+    a.bc = c->bc;
+    a.zchunk = c->zchunk;
+    a.tiles_x = tx;
+    void **from = c->user, **to = c->alt;
+    for (int it = 0; it < n_iters; ++it) {
+        memcpy(a.src, from, sizeof(a.src));
+        memcpy(a.dst, to, sizeof(a.dst));
+        a.partials = (it == n_iters - 1) ? c->partials : nullptr;
+        cudaError_t e = c->precision == THIIM_C128 ? launch_sweep_f64(a, grid, c->stream)
+                                                   : launch_sweep_f32(a, grid, c->stream);
+        if (e != cudaSuccess) return THIIM_ERR_CUDA;
+        void **tmp = from; from = to; to = tmp;
+    }
+    if (from != c->user) {       // odd count: the newest iterate sits in the library's set
+        for (int i = 0; i < THIIM_N_FIELDS; ++i) {
+            if (cudaMemcpyAsync(c->user[i], c->alt[i], c->n_cells * c->elem, cudaMemcpyDeviceToDevice,
+                                c->stream) != cudaSuccess)
+                return THIIM_ERR_CUDA;
+        }
+    }
+    finalize_norms<<<1, 256, 0, c->stream>>>(c->partials, ctas, c->norms);
+    if (cudaGetLastError() != cudaSuccess) return THIIM_ERR_CUDA;
+    c->have_norm = true;
+    return THIIM_OK;
+}
+
+int thiim_residual(thiim_ctx *c, double *rel_residual) {
+    if (!c || !rel_residual) return THIIM_ERR_ARG;
+    if (!c->have_norm) return THIIM_ERR_STATE;
+    double h[2] = {0.0, 0.0};
+    if (cudaMemcpyAsync(h, c->norms, sizeof(h), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
+        return THIIM_ERR_CUDA;
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return THIIM_ERR_CUDA;
+    if (!isfinite(h[0]) || !isfinite(h[1])) return THIIM_ERR_NONFINITE;
+    *rel_residual = h[1] > 0.0 ? sqrt(h[0] / h[1]) : 0.0;
+    return THIIM_OK;
+}
+
+int thiim_build_coeffs(thiim_ctx *c, const void *eps_r, const double *sigma_pml_e,
+                       const double *sigma_pml_h, double omega, double tau, int k_s, double amp_re,
+                       double amp_im, void *const coeff[THIIM_N_COEFFS]) {
+    if (!c || !eps_r || !coeff) return THIIM_ERR_ARG;
+    if (!(tau > 0.0) || !isfinite(omega) || !isfinite(tau) || k_s >= c->nz) return THIIM_ERR_ARG;
+    if (!aligned(eps_r, 16)) return THIIM_ERR_ALIGN;
+    for (int i = 0; i < THIIM_N_COEFFS; ++i) {
+        if (!coeff[i]) return THIIM_ERR_ARG;
+        if (!aligned(coeff[i], c->elem)) return THIIM_ERR_ALIGN;
+    }
+    // Discrete frequency of the fixed point and the incident wave number:
+    // omega_t = 2 sin(omega tau / 2) / tau, 2 sin(kappa / 2) = omega_t.
+    const double wt = 2.0 * sin(0.5 * omega * tau) / tau;
+    if (k_s >= 0 && !(fabs(wt) <= 2.0)) return THIIM_ERR_ARG;
+    if (!c->pml) {
+        if (cudaMalloc(&c->pml, 2 * (size_t)c->nz * sizeof(double)) != cudaSuccess) return THIIM_ERR_NOMEM;
+        if (cudaMalloc(&c->flag, sizeof(int)) != cudaSuccess) return THIIM_ERR_NOMEM;
+    }
+    double *host = (double *)calloc(2 * (size_t)c->nz, sizeof(double));
+    if (!host) return THIIM_ERR_NOMEM;
+    if (sigma_pml_e) memcpy(host, sigma_pml_e, (size_t)c->nz * sizeof(double));
+    if (sigma_pml_h) memcpy(host + c->nz, sigma_pml_h, (size_t)c->nz * sizeof(double));
+    cudaError_t e = cudaMemcpyAsync(c->pml, host, 2 * (size_t)c->nz * sizeof(double), cudaMemcpyHostToDevice,
+                                    c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->flag, 0, sizeof(int), c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);   // host buffer may go away
+    free(host);
+    if (e != cudaSuccess) return THIIM_ERR_CUDA;
+
+    BuildArgs a;
+    memset(&a, 0, sizeof(a));
+    a.eps = (const double2 *)eps_r;
+    a.sig_e = c->pml;
+    a.sig_h = c->pml + c->nz;
+    memcpy(a.co, coeff, sizeof(a.co));
+    a.nx = c->nx; a.ny = c->ny; a.nz = c->nz;
+    a.omega = omega; a.tau = tau;
+    a.k_s = k_s;
+    a.flag = c->flag;
+    if (k_s >= 0) {
+        // Hyx (sign -1) at the scattered-field H plane k_s reads the incident
+        // E_x(k_s) = amp:  Src = +c_Hyx * amp.
+        // Exy (sign -1) at the total-field E plane k_s reads the incident
+        // H_y(k_s) = -(E_inc(k_s) - E_inc(k_s - 1)) / (i omega_t)
+        //          = -amp (1 - e^{i kappa}) / (i omega_t):  Src = +c_Exy * H_y.
+        const double kappa = 2.0 * asin(0.5 * wt);
+        const double dre = 1.0 - cos(kappa), dim = -sin(kappa);   // 1 - e^{i kappa}
+        const double nre = -(amp_re * dre - amp_im * dim), nim = -(amp_re * dim + amp_im * dre);
+        // divide by i omega_t:  (nre + i nim) / (i wt) = (nim - i nre) / wt
+        a.src_h.x = amp_re; a.src_h.y = amp_im;
+        a.src_e.x = nim / wt; a.src_e.y = -nre / wt;
+    }
+    const int threads = 256;
+    long blocks = (long)((c->n_cells + threads - 1) / threads);
+    if (blocks > 32L * c->num_sms) blocks = 32L * c->num_sms;
+    if (c->precision == THIIM_C128)
+        build_coeffs_kernel<double2><<<(unsigned)blocks, threads, 0, c->stream>>>(a);
+    else
+        build_coeffs_kernel<float2><<<(unsigned)blocks, threads, 0, c->stream>>>(a);
+    if (cudaGetLastError() != cudaSuccess) return THIIM_ERR_CUDA;
+    int flag = 0;
+    if (cudaMemcpyAsync(&flag, c->flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess)
+        return THIIM_ERR_CUDA;
+    return flag ? THIIM_ERR_ARG : THIIM_OK;
+}
+
+void thiim_destroy(thiim_ctx *c) {
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    for (int i = 0; i < THIIM_N_FIELDS; ++i)
+        if (c->alt[i]) cudaFree(c->alt[i]);
+    if (c->partials) cudaFree(c->partials);
+    if (c->norms) cudaFree(c->norms);
+    if (c->pml) cudaFree(c->pml);
+    if (c->flag) cudaFree(c->flag);
+    delete c;
+}
+
+}  // extern "C"

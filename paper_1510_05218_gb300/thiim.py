@@ -1,0 +1,220 @@
+"""ctypes binding of the THIIM C ABI (include/thiim.h), same names as the C calls.
+
+Tensors are torch CUDA tensors (complex128 for THIIM_C128, complex64 for
+THIIM_C64), contiguous, in the layout (nz, ny, nx) with x fastest.  Only their
+data pointers cross the ABI.  Errors raise ThiimError with the library's code.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+from . import build as _build
+
+THIIM_C128 = 0
+THIIM_C64 = 1
+THIIM_PERIODIC_X = 1
+THIIM_PERIODIC_Y = 2
+THIIM_PERIODIC_Z = 4
+
+_HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "thiim.h")
+_lib = None
+
+
+class ThiimError(RuntimeError):
+    def __init__(self, call, code):
+        self.code = code
+        msg = "unknown"
+        if _lib is not None:
+            msg = _lib.thiim_strerror(code).decode()
+        super().__init__("%s failed: %s (%d)" % (call, msg, code))
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load_library(build_if_missing: bool = False):
+    """Load libthiim.so; raises if it is missing (no fallback path exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise RuntimeError("libthiim.so is not built (%s); run __graft_entry__.build() or "
+                               "python paper_1510_05218_gb300/build.py" % path)
+        _build.build()
+    lib = ctypes.CDLL(path)
+    vp = ctypes.c_void_p
+    P28 = vp * 28
+    P12 = vp * 12
+    lib.thiim_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                 ctypes.c_uint, vp]
+    lib.thiim_set_stream.argtypes = [vp, vp]
+    lib.thiim_set_coeffs.argtypes = [vp, P28]
+    lib.thiim_set_fields.argtypes = [vp, P12]
+    lib.thiim_iterate.argtypes = [vp, ctypes.c_int]
+    lib.thiim_residual.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
+    lib.thiim_build_coeffs.argtypes = [vp, vp, vp, vp, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                       ctypes.c_double, ctypes.c_double, P28]
+    lib.thiim_destroy.argtypes = [vp]
+    lib.thiim_destroy.restype = None
+    lib.thiim_strerror.argtypes = [ctypes.c_int]
+    lib.thiim_strerror.restype = ctypes.c_char_p
+    lib.thiim_version.argtypes = []
+    for name in ("thiim_create", "thiim_set_stream", "thiim_set_coeffs", "thiim_set_fields", "thiim_iterate",
+                 "thiim_residual", "thiim_build_coeffs", "thiim_version"):
+        getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def declared_symbols():
+    """Names of the functions declared in include/thiim.h."""
+    text = open(_HEADER).read()
+    return sorted(set(re.findall(r"^\s*(?:int|void|const char \*)\s*\*?\s*(thiim_\w+)\s*\(", text, re.M)))
+
+
+def exported_symbols():
+    """Names of the thiim_* functions the built library exports."""
+    lib = load_library()
+    return sorted(n for n in declared_symbols() if hasattr(lib, n))
+
+
+def _check(call, rc):
+    if rc != 0:
+        raise ThiimError(call, rc)
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(int(getattr(stream, "cuda_stream", stream)))
+
+
+def _ptrs(tensors, n, kind):
+    if len(tensors) != n:
+        raise ValueError("need %d %s arrays, got %d" % (n, kind, len(tensors)))
+    arr = (ctypes.c_void_p * n)()
+    for i, t in enumerate(tensors):
+        if hasattr(t, "is_cuda"):
+            if not t.is_cuda or not t.is_contiguous():
+                raise ValueError("%s array %d must be a contiguous CUDA tensor" % (kind, i))
+            arr[i] = t.data_ptr()
+        else:
+            arr[i] = int(t)
+    return arr
+
+
+def thiim_create(nx, ny, nz, precision=THIIM_C128, bc_flags=THIIM_PERIODIC_X | THIIM_PERIODIC_Y, stream=None):
+    lib = load_library()
+    h = ctypes.c_void_p()
+    _check("thiim_create", lib.thiim_create(ctypes.byref(h), int(nx), int(ny), int(nz), int(precision),
+                                            int(bc_flags), _stream_ptr(stream)))
+    return h
+
+
+def thiim_set_stream(ctx, stream=None):
+    _check("thiim_set_stream", load_library().thiim_set_stream(ctx, _stream_ptr(stream)))
+
+
+def thiim_set_coeffs(ctx, coeffs):
+    _check("thiim_set_coeffs", load_library().thiim_set_coeffs(ctx, _ptrs(coeffs, 28, "coefficient")))
+
+
+def thiim_set_fields(ctx, fields):
+    _check("thiim_set_fields", load_library().thiim_set_fields(ctx, _ptrs(fields, 12, "field")))
+
+
+def thiim_iterate(ctx, n_iters):
+    _check("thiim_iterate", load_library().thiim_iterate(ctx, int(n_iters)))
+
+
+def thiim_residual(ctx) -> float:
+    r = ctypes.c_double()
+    _check("thiim_residual", load_library().thiim_residual(ctx, ctypes.byref(r)))
+    return r.value
+
+
+def thiim_build_coeffs(ctx, eps_r, sigma_pml_e, sigma_pml_h, omega, tau, k_s, amp, coeffs):
+    import numpy as np
+    lib = load_library()
+    se = None if sigma_pml_e is None else np.ascontiguousarray(sigma_pml_e, dtype=np.float64)
+    sh = None if sigma_pml_h is None else np.ascontiguousarray(sigma_pml_h, dtype=np.float64)
+    if not (eps_r.is_cuda and eps_r.is_contiguous()):
+        raise ValueError("eps_r must be a contiguous CUDA complex128 tensor")
+    amp = complex(amp)
+    _check("thiim_build_coeffs", lib.thiim_build_coeffs(
+        ctx, ctypes.c_void_p(eps_r.data_ptr()),
+        None if se is None else se.ctypes.data_as(ctypes.c_void_p),
+        None if sh is None else sh.ctypes.data_as(ctypes.c_void_p),
+        float(omega), float(tau), int(k_s), amp.real, amp.imag, _ptrs(coeffs, 28, "coefficient")))
+
+
+def thiim_destroy(ctx):
+    if ctx:
+        load_library().thiim_destroy(ctx)
+
+
+def thiim_strerror(code) -> str:
+    return load_library().thiim_strerror(int(code)).decode()
+
+
+def thiim_version() -> int:
+    return load_library().thiim_version()
+
+
+class Solver:
+    """Owns the torch tensors of one THIIM problem and a library context.
+
+    fields: 12 tensors, coeffs: 28 tensors, shape (nz, ny, nx), complex128 or
+    complex64 on the current CUDA device.
+    """
+
+    def __init__(self, nx, ny, nz, precision=THIIM_C128, bc=THIIM_PERIODIC_X | THIIM_PERIODIC_Y,
+                 stream=None, device=None):
+        import torch
+        self.nx, self.ny, self.nz = nx, ny, nz
+        self.precision = precision
+        self.dtype = torch.complex128 if precision == THIIM_C128 else torch.complex64
+        self.device = torch.device(device or "cuda")
+        self.ctx = thiim_create(nx, ny, nz, precision, bc, stream)
+        self.fields = None
+        self.coeffs = None
+
+    def _empty(self, n):
+        import torch
+        return [torch.zeros((self.nz, self.ny, self.nx), dtype=self.dtype, device=self.device) for _ in range(n)]
+
+    def set_coeffs(self, coeffs):
+        self.coeffs = list(coeffs)
+        thiim_set_coeffs(self.ctx, self.coeffs)
+
+    def set_fields(self, fields=None):
+        self.fields = list(fields) if fields is not None else self._empty(12)
+        thiim_set_fields(self.ctx, self.fields)
+
+    def build_coeffs(self, eps_r, sigma_pml_e, sigma_pml_h, omega, tau, k_s, amp=1.0):
+        coeffs = self.coeffs if self.coeffs is not None else self._empty(28)
+        thiim_build_coeffs(self.ctx, eps_r, sigma_pml_e, sigma_pml_h, omega, tau, k_s, amp, coeffs)
+        self.set_coeffs(coeffs)
+
+    def iterate(self, n):
+        thiim_iterate(self.ctx, n)
+
+    def residual(self) -> float:
+        return thiim_residual(self.ctx)
+
+    def close(self):
+        if self.ctx:
+            thiim_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
