@@ -176,6 +176,7 @@ def stack_config(name: str) -> LayeredStack:
                 lambda = 320, absorbing layers 96 cells.
     stack256    the stack512 structure at 256^3 (scale 8).
     adjoint128  128^3, scale 4, texture confined to x, y in [48, 80).
+    stackN      any other N: the 32^3 stack scaled by N/32.
     """
     if name == "stack32":
         return LayeredStack(32, 32, 32, lam=20.0, n_sin=4, amp=4.0, seed=0)
@@ -188,6 +189,11 @@ def stack_config(name: str) -> LayeredStack:
     if name == "adjoint128":
         return LayeredStack(128, 128, 128, lam=80.0, n_sin=4, amp=16.0, seed=0,
                             texture_box=(48, 80, 48, 80))
+    if name.startswith("stack") and name[5:].isdigit():
+        # stackN: the 32^3 stack scaled to N^3 (wavelength and every z length x N/32)
+        n = int(name[5:])
+        return LayeredStack(n, n, n, lam=20.0 * n / 32.0, n_sin=16 if n >= 256 else 4,
+                            amp=4.0 * n / 32.0, seed=0)
     raise KeyError(name)
 
 
