@@ -162,6 +162,33 @@ int thiim_build_coeffs(thiim_ctx *ctx, const void *eps_r,
                        double omega, double tau, int k_s, double amp_re,
                        double amp_im, void *const coeff[THIIM_N_COEFFS]);
 
+/*
+ * thiim_step_noalloc — one THIIM iteration that allocates no memory.
+ *   For callers that cannot call cudaMalloc (code running under another
+ *   framework's memory pool or allocator hooks, or with all device memory
+ *   reserved up front).  The paper has no counterpart; this is a deployment
+ *   variant of thiim_iterate for a single iteration.
+ *   src: 12 field arrays holding x^n (read only); dst: 12 other field arrays
+ *   that receive x^{n+1} (no array may appear in both); coeff: 28 arrays;
+ *   all device pointers in the layout above.  cuda_stream: cudaStream_t.
+ *   rel_residual: if non-NULL, the call synchronises the stream and returns
+ *   the relative full-field update of this iteration (as thiim_residual);
+ *   if NULL, the call only enqueues the sweep and returns.
+ *   Scratch: the reduction partials live in one fixed device array of
+ *   16384 CTAs x 16 B (+16 B) = 256 KiB, defined in the library and held by
+ *   every GPU that loads it until the process exits.  A grid needing more
+ *   than 16384 CTAs of 32 x 8 cells (nx/32 * ny/8 > 16384) is rejected with
+ *   THIIM_ERR_ARG.  The first call on a device looks up the array's device
+ *   address; make that first call before any stream capture.  All calls
+ *   share the array, so calls whose GPU work overlaps (other streams or
+ *   host threads on the same device) race on it.
+ * Errors: THIIM_ERR_ARG, THIIM_ERR_ALIGN, THIIM_ERR_CUDA, THIIM_ERR_NONFINITE.
+ */
+int thiim_step_noalloc(int nx, int ny, int nz, int precision, unsigned bc_flags,
+                       void *const src[THIIM_N_FIELDS], void *const dst[THIIM_N_FIELDS],
+                       void *const coeff[THIIM_N_COEFFS], void *cuda_stream,
+                       double *rel_residual);
+
 /* Release the context and its scratch (synchronises the stream first). */
 void thiim_destroy(thiim_ctx *ctx);
 

@@ -59,6 +59,9 @@ def load_library(build_if_missing: bool = False):
     lib.thiim_residual.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
     lib.thiim_build_coeffs.argtypes = [vp, vp, vp, vp, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                        ctypes.c_double, ctypes.c_double, P28]
+    lib.thiim_step_noalloc.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_uint,
+                                       P12, P12, P28, vp, ctypes.POINTER(ctypes.c_double)]
+    lib.thiim_step_noalloc.restype = ctypes.c_int
     lib.thiim_destroy.argtypes = [vp]
     lib.thiim_destroy.restype = None
     lib.thiim_strerror.argtypes = [ctypes.c_int]
@@ -152,6 +155,17 @@ def thiim_build_coeffs(ctx, eps_r, sigma_pml_e, sigma_pml_h, omega, tau, k_s, am
         None if se is None else se.ctypes.data_as(ctypes.c_void_p),
         None if sh is None else sh.ctypes.data_as(ctypes.c_void_p),
         float(omega), float(tau), int(k_s), amp.real, amp.imag, _ptrs(coeffs, 28, "coefficient")))
+
+
+def thiim_step_noalloc(nx, ny, nz, precision, bc_flags, src, dst, coeffs, stream=None, want_residual=True):
+    """One iteration src -> dst without any allocation; returns the residual or None."""
+    r = ctypes.c_double()
+    rc = load_library().thiim_step_noalloc(int(nx), int(ny), int(nz), int(precision), int(bc_flags),
+                                           _ptrs(src, 12, "field"), _ptrs(dst, 12, "field"),
+                                           _ptrs(coeffs, 28, "coefficient"), _stream_ptr(stream),
+                                           ctypes.byref(r) if want_residual else None)
+    _check("thiim_step_noalloc", rc)
+    return r.value if want_residual else None
 
 
 def thiim_destroy(ctx):
