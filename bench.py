@@ -28,7 +28,11 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "THIIM E+H MLUP/s at 512^3 and % of HBM roofline; complex64 vs FP64 at ≤1e-6"
-BYTES_PER_LUP = {"c128": 52 * 16, "c64": 52 * 8}   # 40 arrays read + 12 written per cell
+BYTES_PER_LUP = {"c128": 52 * 16, "pair": 52 * 16, "c64": 52 * 8}   # 40 arrays read + 12 written per cell
+DTYPE = {"c128": "f64", "pair": "f32x2", "c64": "f32"}
+PRECISION_CODE = {"c128": 0, "c64": 1, "pair": 2}
+KERNEL = {"c128": "sweep_kernel<Native<double>>", "pair": "sweep_kernel<PairArith<1,1>>",
+          "c64": "sweep_kernel<Native<float>>"}
 FLOPS_PER_LUP = 248                                  # the paper's count (Sec. III-A)
 SWEEP_SRC = os.path.join(ROOT, "paper_1510_05218_gb300", "csrc", "thiim_sweep.cuh")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "sweep_traffic.json")
@@ -197,8 +201,8 @@ def run_ours(args):
     p.load_library()
 
     st = stack_config(args.workload)
-    prec = p.THIIM_C128 if args.precision == "c128" else p.THIIM_C64
-    dt = torch.complex128 if prec == p.THIIM_C128 else torch.complex64
+    prec = PRECISION_CODE[args.precision]
+    dt = torch.complex64 if prec == p.THIIM_C64 else torch.complex128
     shape = (st.nz, st.ny, st.nx)
     cells = st.nx * st.ny * st.nz
     iters = args.iters
@@ -262,7 +266,7 @@ def run_ours(args):
     alg_bytes = BYTES_PER_LUP[args.precision] * cells
     peak, peak_kind = _peaks()
     achieved = alg_bytes / launch_s / 1e9
-    kernel_key = "sweep_kernel<%s>" % ("double" if args.precision == "c128" else "float")
+    kernel_key = KERNEL[args.precision]
     traffic = _traffic(kernel_key, cells)
 
     # --- end to end through the public API with host buffers --------------
@@ -319,7 +323,7 @@ def run_ours(args):
     out = {
         "metric": METRIC, "value": value, "unit": "MLUP/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64" if args.precision == "c128" else "f32", "data": "synthetic",
+        "vs_baseline": None, "dtype": DTYPE[args.precision], "data": "synthetic",
         "config": {"workload": "%s: %dx%dx%d textured thin-film stack (seeded sinusoid texture), %s, "
                                "%d THIIM iterations + FP64 residual per step" % (
                                    args.workload, st.nx, st.ny, st.nz, args.precision, iters),
@@ -351,7 +355,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="stack512")
-    ap.add_argument("--precision", default="c128", choices=["c128", "c64"])
+    ap.add_argument("--precision", default="c128", choices=["c128", "pair", "c64"])
     ap.add_argument("--iters", type=int, default=200)
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--e2e-warmup", type=int, default=1)

@@ -14,8 +14,8 @@
  * Grid:    nx * ny * nz cells; cell (i, j, k) is element (k*ny + j)*nx + i
  *          of every array (x fastest, the layout of Listing 1).
  * Arrays:  contiguous complex values, interleaved (re, im):
- *          THIIM_C128 -> 16-byte double complex, 16-byte aligned;
- *          THIIM_C64  ->  8-byte float complex,   8-byte aligned.
+ *          THIIM_C128, THIIM_C128_PAIR -> 16-byte double complex, 16-byte aligned;
+ *          THIIM_C64                   ->  8-byte float complex,   8-byte aligned.
  * Fields:  12 splits, in this order (split F_ab of component a reads
  *          component b of the other field, as in Listings 1-2):
  *            Hxy Hxz Hyx Hyz Hzx Hzy Exy Exz Eyx Eyz Ezx Ezy
@@ -57,8 +57,10 @@ extern "C" {
 typedef struct thiim_ctx thiim_ctx;
 
 enum thiim_precision {
-    THIIM_C128 = 0, /* complex128 storage, FP64 arithmetic */
-    THIIM_C64 = 1   /* complex64 storage, FP32 arithmetic */
+    THIIM_C128 = 0,     /* complex128 storage, FP64 arithmetic */
+    THIIM_C64 = 1,      /* complex64 storage, FP32 arithmetic */
+    THIIM_C128_PAIR = 2 /* complex128 storage, arithmetic on FP32 pairs
+                           (hi + lo, ~2^-48 relative per operation) */
 };
 
 enum thiim_bc_flags {
@@ -102,6 +104,10 @@ int thiim_set_stream(thiim_ctx *ctx, void *cuda_stream);
  * thiim_set_coeffs — borrow the 28 coefficient arrays (device pointers, in the
  * context's precision, layout above).  Errors: THIIM_ERR_ARG on NULL,
  * THIIM_ERR_ALIGN on misalignment.
+ * THIIM_C128_PAIR: the next thiim_iterate splits the coefficients into FP32
+ * pairs held by the library (28 more arrays of the same size) and reuses the
+ * split until thiim_set_coeffs or thiim_build_coeffs is called again; call
+ * one of them after changing the arrays' contents.
  */
 int thiim_set_coeffs(thiim_ctx *ctx, void *const coeff[THIIM_N_COEFFS]);
 
@@ -116,7 +122,10 @@ int thiim_set_fields(thiim_ctx *ctx, void *const field[THIIM_N_FIELDS]);
 /*
  * thiim_iterate — enqueue n_iters THIIM iterations (Eqs. 3-5): each is the
  * six H half-step updates followed by the six E updates.  When it completes
- * on the stream, the caller's field arrays hold x^{n + n_iters}.  The last
+ * on the stream, the caller's field arrays hold x^{n + n_iters}.  Under
+ * THIIM_C128_PAIR the intermediate iterates of one call are kept as FP32
+ * pairs (in the caller's and the library's field arrays) and only the final
+ * one is written as complex128.  The last
  * iteration also accumulates, in FP64, the norms that thiim_residual reports.
  * n_iters = 0 does nothing.  Errors: THIIM_ERR_STATE if fields or
  * coefficients are missing, THIIM_ERR_ARG if n_iters < 0, THIIM_ERR_CUDA.

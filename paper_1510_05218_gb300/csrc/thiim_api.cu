@@ -25,6 +25,8 @@ struct thiim_ctx {
     void *coeff[THIIM_N_COEFFS];
     void *user[THIIM_N_FIELDS];  // caller's field arrays (hold x^n between calls)
     void *alt[THIIM_N_FIELDS];   // library's second field set
+    void *pair_co[THIIM_N_COEFFS];  // THIIM_C128_PAIR: coefficients split into float4 pairs
+    bool pair_dirty;             // coefficients changed since they were last split
     bool have_coeffs, have_fields, have_norm;
     int zchunk;                  // planes per CTA of the sweep
     double *partials;            // 2 doubles per sweep CTA
@@ -196,7 +198,7 @@ int thiim_create(thiim_ctx **out, int nx, int ny, int nz, int precision, unsigne
     *out = nullptr;
     if (nx < 1 || ny < 1 || nz < 1) return THIIM_ERR_ARG;
     if ((double)nx * ny * nz > (double)(1ull << 40)) return THIIM_ERR_ARG;
-    if (precision != THIIM_C128 && precision != THIIM_C64) return THIIM_ERR_ARG;
+    if (precision != THIIM_C128 && precision != THIIM_C64 && precision != THIIM_C128_PAIR) return THIIM_ERR_ARG;
     if (bc_flags & ~7u) return THIIM_ERR_ARG;
     thiim_ctx *c = new (std::nothrow) thiim_ctx();
     if (!c) return THIIM_ERR_NOMEM;
@@ -204,7 +206,7 @@ int thiim_create(thiim_ctx **out, int nx, int ny, int nz, int precision, unsigne
     c->precision = precision;
     c->bc = bc_flags;
     c->stream = (cudaStream_t)cuda_stream;
-    c->elem = precision == THIIM_C128 ? 16 : 8;
+    c->elem = precision == THIIM_C64 ? 8 : 16;
     c->n_cells = (size_t)nx * ny * nz;
     if (cudaGetDevice(&c->device) != cudaSuccess ||
         cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) {
@@ -230,6 +232,7 @@ int thiim_set_coeffs(thiim_ctx *c, void *const coeff[THIIM_N_COEFFS]) {
     }
     memcpy(c->coeff, coeff, sizeof(c->coeff));
     c->have_coeffs = true;
+    c->pair_dirty = true;
     return THIIM_OK;
 }
 
@@ -267,9 +270,29 @@ int thiim_iterate(thiim_ctx *c, int n_iters) {
     if (st) return st;
     if (!c->norms && cudaMalloc(&c->norms, 2 * sizeof(double)) != cudaSuccess) return THIIM_ERR_NOMEM;
 
+    const bool pair = c->precision == THIIM_C128_PAIR;
+    if (pair) {
+        if (!c->pair_co[0]) {
+            for (int i = 0; i < THIIM_N_COEFFS; ++i) {
+                if (cudaMalloc(&c->pair_co[i], c->n_cells * 16) != cudaSuccess) {
+                    for (int j = 0; j < i; ++j) { cudaFree(c->pair_co[j]); c->pair_co[j] = nullptr; }
+                    c->pair_co[i] = nullptr;
+                    cudaGetLastError();
+                    return THIIM_ERR_NOMEM;
+                }
+            }
+            c->pair_dirty = true;
+        }
+        if (c->pair_dirty) {
+            if (split_coeffs(c->coeff, c->pair_co, THIIM_N_COEFFS, c->n_cells, c->stream) != cudaSuccess)
+                return THIIM_ERR_CUDA;
+            c->pair_dirty = false;
+        }
+    }
+
     SweepArgs a;
     memset(&a, 0, sizeof(a));
-    memcpy(a.co, c->coeff, sizeof(a.co));
+    memcpy(a.co, pair ? c->pair_co : c->coeff, sizeof(a.co));
     a.nx = c->nx; a.ny = c->ny; a.nz = c->nz;
     a.bc = c->bc;
     a.zchunk = c->zchunk;
@@ -279,8 +302,13 @@ int thiim_iterate(thiim_ctx *c, int n_iters) {
         memcpy(a.src, from, sizeof(a.src));
         memcpy(a.dst, to, sizeof(a.dst));
         a.partials = (it == n_iters - 1) ? c->partials : nullptr;
-        cudaError_t e = c->precision == THIIM_C128 ? launch_sweep_f64(a, grid, c->stream)
-                                                   : launch_sweep_f32(a, grid, c->stream);
+        cudaError_t e;
+        if (pair)   // intermediate iterates stay as float4 pairs; first reads and last writes complex128
+            e = launch_sweep_pair(a, grid, c->stream, it > 0, it < n_iters - 1);
+        else if (c->precision == THIIM_C128)
+            e = launch_sweep_f64(a, grid, c->stream);
+        else
+            e = launch_sweep_f32(a, grid, c->stream);
         if (e != cudaSuccess) return THIIM_ERR_CUDA;
         void **tmp = from; from = to; to = tmp;
     }
@@ -364,7 +392,8 @@ int thiim_build_coeffs(thiim_ctx *c, const void *eps_r, const double *sigma_pml_
     const int threads = 256;
     long blocks = (long)((c->n_cells + threads - 1) / threads);
     if (blocks > 32L * c->num_sms) blocks = 32L * c->num_sms;
-    if (c->precision == THIIM_C128)
+    c->pair_dirty = true;
+    if (c->precision != THIIM_C64)
         build_coeffs_kernel<double2><<<(unsigned)blocks, threads, 0, c->stream>>>(a);
     else
         build_coeffs_kernel<float2><<<(unsigned)blocks, threads, 0, c->stream>>>(a);
@@ -381,6 +410,8 @@ void thiim_destroy(thiim_ctx *c) {
     cudaStreamSynchronize(c->stream);
     for (int i = 0; i < THIIM_N_FIELDS; ++i)
         if (c->alt[i]) cudaFree(c->alt[i]);
+    for (int i = 0; i < THIIM_N_COEFFS; ++i)
+        if (c->pair_co[i]) cudaFree(c->pair_co[i]);
     if (c->partials) cudaFree(c->partials);
     if (c->norms) cudaFree(c->norms);
     if (c->pml) cudaFree(c->pml);

@@ -1,0 +1,180 @@
+// Arithmetic policies of the fused sweep.
+//
+// The sweep body (thiim_sweep.cuh) is written once against a policy that
+// says how a complex value is loaded, stored, added and updated:
+//
+//   Native<double>  complex128 storage, FP64 arithmetic.
+//   Native<float>   complex64 storage, FP32 arithmetic.
+//   PairArith<I,O>  complex128 data, arithmetic on pairs of FP32 numbers
+//                   (hi + lo, "double-float").  GB300 executes FP64 at
+//                   2 instructions/clk/SM but FP32 at 128, so the FP64 sweep
+//                   is pipe-bound; the pair form moves the work to the FP32
+//                   pipe.  Coefficients arrive pre-split as float4
+//                   (re.hi, re.lo, im.hi, im.lo); fields are read as
+//                   complex128 (I = 0) or as float4 pairs (I = 1) and written
+//                   as complex128 (O = 0) or pairs (O = 1), so a multi-
+//                   iteration call converts only on its first and last pass.
+//
+// Pair arithmetic (Dekker / Knuth error-free transformations):
+//   two_sum(a, b)  -> s + e == a + b exactly (6 FP32 operations),
+//   two_prod(a, b) -> p + e == a * b exactly (1 multiply + 1 FMA),
+// so a product of pairs is exact up to the lo*lo term and the cross terms'
+// rounding (relative 2^-48), and a sum of such products is accumulated with
+// two_sum on the leading parts and plain FP32 on the error parts.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace thiim {
+
+template <typename R> struct cplx_of;
+template <> struct cplx_of<double> { typedef double2 type; };
+template <> struct cplx_of<float> { typedef float2 type; };
+
+template <typename V>
+__device__ __forceinline__ V ldg_as(const void *base, size_t i) {
+    return __ldg(reinterpret_cast<const V *>(base) + i);
+}
+template <typename V>
+__device__ __forceinline__ void stg_as(void *base, size_t i, V v) {
+    reinterpret_cast<V *>(base)[i] = v;
+}
+
+// ---------------------------------------------------------------- native ----
+template <typename R>
+struct Native {
+    typedef typename cplx_of<R>::type Z;
+    static constexpr bool pairs = false;
+    __device__ static __forceinline__ Z zero() { Z z; z.x = R(0); z.y = R(0); return z; }
+    __device__ static __forceinline__ Z ld_field(const void *b, size_t i) { return ldg_as<Z>(b, i); }
+    __device__ static __forceinline__ Z ld_coef(const void *b, size_t i) { return ldg_as<Z>(b, i); }
+    __device__ static __forceinline__ void st_field(void *b, size_t i, Z v) { stg_as<Z>(b, i, v); }
+    __device__ static __forceinline__ Z add(Z a, Z b) { Z r; r.x = a.x + b.x; r.y = a.y + b.y; return r; }
+    __device__ static __forceinline__ Z sub(Z a, Z b) { Z r; r.x = a.x - b.x; r.y = a.y - b.y; return r; }
+    // t*x + s + c*d (d carries the curl sign)
+    __device__ static __forceinline__ Z upd_src(Z x, Z t, Z c, Z d, Z s) {
+        Z r;
+        r.x = fma(t.x, x.x, s.x); r.x = fma(-t.y, x.y, r.x); r.x = fma(c.x, d.x, r.x); r.x = fma(-c.y, d.y, r.x);
+        r.y = fma(t.x, x.y, s.y); r.y = fma(t.y, x.x, r.y); r.y = fma(c.x, d.y, r.y); r.y = fma(c.y, d.x, r.y);
+        return r;
+    }
+    __device__ static __forceinline__ Z upd(Z x, Z t, Z c, Z d) {
+        Z r;
+        r.x = t.x * x.x; r.x = fma(-t.y, x.y, r.x); r.x = fma(c.x, d.x, r.x); r.x = fma(-c.y, d.y, r.x);
+        r.y = t.x * x.y; r.y = fma(t.y, x.x, r.y); r.y = fma(c.x, d.y, r.y); r.y = fma(c.y, d.x, r.y);
+        return r;
+    }
+    __device__ static __forceinline__ double re(Z a) { return (double)a.x; }
+    __device__ static __forceinline__ double im(Z a) { return (double)a.y; }
+};
+
+// ------------------------------------------------------------ FP32 pairs ----
+struct fpair { float h, l; };
+struct zpair { fpair x, y; };   // complex: real pair, imaginary pair
+
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+// a + b, leading part exact, error part not renormalised
+__device__ __forceinline__ fpair p_add(fpair a, fpair b) {
+    fpair r;
+    float e;
+    two_sum(a.h, b.h, r.h, e);
+    r.l = e + (a.l + b.l);
+    return r;
+}
+__device__ __forceinline__ fpair p_sub(fpair a, fpair b) {
+    fpair r;
+    float e;
+    two_sum(a.h, -b.h, r.h, e);
+    r.l = e + (a.l - b.l);
+    return r;
+}
+
+// Accumulates a sum of products of pairs: leading parts exactly (two_sum),
+// error parts in plain FP32.
+struct pacc {
+    float s, lo;
+    __device__ __forceinline__ void first(float ah, float al, float bh, float bl) {
+        s = ah * bh;
+        lo = fmaf(ah, bh, -s);
+        lo = fmaf(ah, bl, lo);
+        lo = fmaf(al, bh, lo);
+    }
+    __device__ __forceinline__ void prod(float ah, float al, float bh, float bl) {
+        const float p = ah * bh;
+        float e = fmaf(ah, bh, -p);
+        e = fmaf(ah, bl, e);
+        e = fmaf(al, bh, e);
+        float t;
+        two_sum(s, p, s, t);
+        lo += t + e;
+    }
+    __device__ __forceinline__ void term(fpair v) {
+        float t;
+        two_sum(s, v.h, s, t);
+        lo += t + v.l;
+    }
+    __device__ __forceinline__ fpair result() const {   // renormalised
+        fpair r;
+        r.h = s + lo;
+        r.l = lo - (r.h - s);
+        return r;
+    }
+};
+
+__device__ __forceinline__ fpair split_double(double d) {
+    fpair r;
+    r.h = __double2float_rn(d);
+    r.l = __double2float_rn(d - (double)r.h);
+    return r;
+}
+
+template <int IN_PAIRS, int OUT_PAIRS>
+struct PairArith {
+    typedef zpair Z;
+    static constexpr bool pairs = true;
+    __device__ static __forceinline__ Z zero() { Z z; z.x.h = z.x.l = z.y.h = z.y.l = 0.f; return z; }
+    __device__ static __forceinline__ Z from_f4(float4 v) { Z z; z.x.h = v.x; z.x.l = v.y; z.y.h = v.z; z.y.l = v.w; return z; }
+    __device__ static __forceinline__ Z ld_field(const void *b, size_t i) {
+        if (IN_PAIRS) return from_f4(ldg_as<float4>(b, i));
+        const double2 v = ldg_as<double2>(b, i);
+        Z z; z.x = split_double(v.x); z.y = split_double(v.y);
+        return z;
+    }
+    __device__ static __forceinline__ Z ld_coef(const void *b, size_t i) { return from_f4(ldg_as<float4>(b, i)); }
+    __device__ static __forceinline__ void st_field(void *b, size_t i, Z v) {
+        if (OUT_PAIRS) {
+            stg_as<float4>(b, i, make_float4(v.x.h, v.x.l, v.y.h, v.y.l));
+        } else {
+            stg_as<double2>(b, i, make_double2(re(v), im(v)));
+        }
+    }
+    __device__ static __forceinline__ Z add(Z a, Z b) { Z r; r.x = p_add(a.x, b.x); r.y = p_add(a.y, b.y); return r; }
+    __device__ static __forceinline__ Z sub(Z a, Z b) { Z r; r.x = p_sub(a.x, b.x); r.y = p_sub(a.y, b.y); return r; }
+    // t*x + s + c*d: real = tr xr - ti xi + cr dr - ci di (+ sr); imag = tr xi + ti xr + cr di + ci dr (+ si)
+    __device__ static __forceinline__ Z upd_impl(Z x, Z t, Z c, Z d, const Z *s) {
+        pacc r, q;
+        r.first(t.x.h, t.x.l, x.x.h, x.x.l);
+        r.prod(-t.y.h, -t.y.l, x.y.h, x.y.l);
+        r.prod(c.x.h, c.x.l, d.x.h, d.x.l);
+        r.prod(-c.y.h, -c.y.l, d.y.h, d.y.l);
+        q.first(t.x.h, t.x.l, x.y.h, x.y.l);
+        q.prod(t.y.h, t.y.l, x.x.h, x.x.l);
+        q.prod(c.x.h, c.x.l, d.y.h, d.y.l);
+        q.prod(c.y.h, c.y.l, d.x.h, d.x.l);
+        if (s) { r.term(s->x); q.term(s->y); }
+        Z z; z.x = r.result(); z.y = q.result();
+        return z;
+    }
+    __device__ static __forceinline__ Z upd_src(Z x, Z t, Z c, Z d, Z s) { return upd_impl(x, t, c, d, &s); }
+    __device__ static __forceinline__ Z upd(Z x, Z t, Z c, Z d) { return upd_impl(x, t, c, d, nullptr); }
+    __device__ static __forceinline__ double re(Z a) { return (double)a.x.h + (double)a.x.l; }
+    __device__ static __forceinline__ double im(Z a) { return (double)a.y.h + (double)a.y.l; }
+};
+
+}  // namespace thiim

@@ -15,16 +15,17 @@
 // Per cell and iteration the compulsory traffic is 40 arrays read (12 fields
 // + 28 coefficients) and 12 written: 52 x 16 B = 832 B in FP64 and 416 B in
 // FP32 (the paper's naive code moves 1344 B, Eq. 8).
+//
+// The arithmetic is a policy A (thiim_arith.cuh): native FP64, native FP32,
+// or FP32 pairs on complex128 data.
 #pragma once
 
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-namespace thiim {
+#include "thiim_arith.cuh"
 
-template <typename R> struct cplx_of;
-template <> struct cplx_of<double> { typedef double2 type; };
-template <> struct cplx_of<float> { typedef float2 type; };
+namespace thiim {
 
 // Field order: Hxy Hxz Hyx Hyz Hzx Hzy Exy Exz Eyx Eyz Ezx Ezy.
 enum { HXY, HXZ, HYX, HYZ, HZX, HZY, EXY, EXZ, EYX, EYZ, EZX, EZY };
@@ -42,37 +43,7 @@ struct SweepArgs {
     double *partials;      // 2 doubles per CTA (|dF|^2, |F|^2) or nullptr
 };
 
-template <typename V>
-__device__ __forceinline__ V cadd(V a, V b) { V r; r.x = a.x + b.x; r.y = a.y + b.y; return r; }
-template <typename V>
-__device__ __forceinline__ V csub(V a, V b) { V r; r.x = a.x - b.x; r.y = a.y - b.y; return r; }
-
-// t*x + src + c*d  (d already carries the curl sign)
-template <typename V>
-__device__ __forceinline__ V upd_src(V x, V t, V c, V d, V s) {
-    V r;
-    r.x = fma(t.x, x.x, s.x); r.x = fma(-t.y, x.y, r.x); r.x = fma(c.x, d.x, r.x); r.x = fma(-c.y, d.y, r.x);
-    r.y = fma(t.x, x.y, s.y); r.y = fma(t.y, x.x, r.y); r.y = fma(c.x, d.y, r.y); r.y = fma(c.y, d.x, r.y);
-    return r;
-}
-template <typename V>
-__device__ __forceinline__ V upd(V x, V t, V c, V d) {
-    V r;
-    r.x = t.x * x.x; r.x = fma(-t.y, x.y, r.x); r.x = fma(c.x, d.x, r.x); r.x = fma(-c.y, d.y, r.x);
-    r.y = t.x * x.y; r.y = fma(t.y, x.x, r.y); r.y = fma(c.x, d.y, r.y); r.y = fma(c.y, d.x, r.y);
-    return r;
-}
-
-template <typename V>
-__device__ __forceinline__ V ldg(const void *base, size_t i) {
-    return __ldg(reinterpret_cast<const V *>(base) + i);
-}
-template <typename V>
-__device__ __forceinline__ void stg(void *base, size_t i, V v) {
-    reinterpret_cast<V *>(base)[i] = v;
-}
-
-template <typename V> struct Vec3 { V x, y, z; };
+template <typename Z> struct Vec3 { Z x, y, z; };
 
 // Map a halo coordinate g in [-1, n] into the grid; false if outside a
 // non-periodic edge.
@@ -82,14 +53,25 @@ __device__ __forceinline__ bool wrap(int &g, int n, bool periodic) {
     return true;
 }
 
-template <typename R, int TX, int TY, int NT>
+template <typename A>
+__device__ __forceinline__ double norm2(typename A::Z a) {
+    const double x = A::re(a), y = A::im(a);
+    return x * x + y * y;
+}
+template <typename A>
+__device__ __forceinline__ double dnorm2(typename A::Z a, typename A::Z b) {
+    const double x = A::re(a) - A::re(b), y = A::im(a) - A::im(b);
+    return x * x + y * y;
+}
+
+template <typename A, int TX, int TY, int NT>
 __global__ void __launch_bounds__(NT)
 sweep_kernel(const SweepArgs a) {
-    typedef typename cplx_of<R>::type V;
+    typedef typename A::Z Z;
     constexpr int EW = TX + 2, EH = TY + 2;   // E^n region: -1 .. TX (x), -1 .. TY (y)
     constexpr int HW = TX + 1, HH = TY + 1;   // new-H region: 0 .. TX, 0 .. TY
-    __shared__ Vec3<V> sE[2][EH][EW];         // full E^n at planes k (cur) and k-1
-    __shared__ Vec3<V> sH[2][HH][HW];         // full new H at planes k (cur) and k-1
+    __shared__ Vec3<Z> sE[2][EH][EW];         // full E^n at planes k (cur) and k-1
+    __shared__ Vec3<Z> sH[2][HH][HW];         // full new H at planes k (cur) and k-1
     __shared__ double red[2][NT / 32];
 
     const int nx = a.nx, ny = a.ny, nz = a.nz;
@@ -115,13 +97,13 @@ sweep_kernel(const SweepArgs a) {
         for (int w = threadIdx.x; w < ecount; w += NT) {
             const int tx = w % ew, ty = w / ew;
             int gx = i0 - 1 + tx, gy = j0 - 1 + ty;
-            Vec3<V> f;
-            f.x.x = f.x.y = f.y.x = f.y.y = f.z.x = f.z.y = R(0);
+            Vec3<Z> f;
+            f.x = f.y = f.z = A::zero();
             if (zin && wrap(gx, nx, px) && wrap(gy, ny, py)) {
                 const size_t p = (size_t)kk * plane + (size_t)gy * nx + gx;
-                f.x = cadd(ldg<V>(a.src[EXY], p), ldg<V>(a.src[EXZ], p));
-                f.y = cadd(ldg<V>(a.src[EYX], p), ldg<V>(a.src[EYZ], p));
-                f.z = cadd(ldg<V>(a.src[EZX], p), ldg<V>(a.src[EZY], p));
+                f.x = A::add(A::ld_field(a.src[EXY], p), A::ld_field(a.src[EXZ], p));
+                f.y = A::add(A::ld_field(a.src[EYX], p), A::ld_field(a.src[EYZ], p));
+                f.z = A::add(A::ld_field(a.src[EZX], p), A::ld_field(a.src[EZY], p));
             }
             sE[b][ty][tx] = f;
         }
@@ -141,45 +123,41 @@ sweep_kernel(const SweepArgs a) {
         for (int w = threadIdx.x; w < hcount; w += NT) {
             const int hx = w % hw, hy = w / hw;
             int gx = i0 + hx, gy = j0 + hy;
-            Vec3<V> hn;
-            hn.x.x = hn.x.y = hn.y.x = hn.y.y = hn.z.x = hn.z.y = R(0);
+            Vec3<Z> hn;
+            hn.x = hn.y = hn.z = A::zero();
             if (!beyond && wrap(gx, nx, px) && wrap(gy, ny, py)) {
                 const size_t p = (size_t)kk * plane + (size_t)gy * nx + gx;
-                const Vec3<V> e0 = sE[cur][hy + 1][hx + 1];
-                const Vec3<V> exm = sE[cur][hy + 1][hx];
-                const Vec3<V> eym = sE[cur][hy][hx + 1];
-                const Vec3<V> ezm = sE[prev][hy + 1][hx + 1];
+                const Vec3<Z> e0 = sE[cur][hy + 1][hx + 1];
+                const Vec3<Z> exm = sE[cur][hy + 1][hx];
+                const Vec3<Z> eym = sE[cur][hy][hx + 1];
+                const Vec3<Z> ezm = sE[prev][hy + 1][hx + 1];
                 // backward differences; the curl sign is folded into the order
-                const V dHxy = csub(e0.y, ezm.y);   // +dz Ey
-                const V dHxz = csub(eym.z, e0.z);   // -dy Ez
-                const V dHyx = csub(ezm.x, e0.x);   // -dz Ex
-                const V dHyz = csub(e0.z, exm.z);   // +dx Ez
-                const V dHzx = csub(e0.x, eym.x);   // +dy Ex
-                const V dHzy = csub(exm.y, e0.y);   // -dx Ey
-                const V oxy = ldg<V>(a.src[HXY], p), oxz = ldg<V>(a.src[HXZ], p);
-                const V oyx = ldg<V>(a.src[HYX], p), oyz = ldg<V>(a.src[HYZ], p);
-                const V ozx = ldg<V>(a.src[HZX], p), ozy = ldg<V>(a.src[HZY], p);
-                const V nxy = upd_src(oxy, ldg<V>(a.co[T0 + HXY], p), ldg<V>(a.co[C0 + HXY], p), dHxy, ldg<V>(a.co[SRC_HXY], p));
-                const V nxz = upd(oxz, ldg<V>(a.co[T0 + HXZ], p), ldg<V>(a.co[C0 + HXZ], p), dHxz);
-                const V nyx = upd_src(oyx, ldg<V>(a.co[T0 + HYX], p), ldg<V>(a.co[C0 + HYX], p), dHyx, ldg<V>(a.co[SRC_HYX], p));
-                const V nyz = upd(oyz, ldg<V>(a.co[T0 + HYZ], p), ldg<V>(a.co[C0 + HYZ], p), dHyz);
-                const V nzx = upd(ozx, ldg<V>(a.co[T0 + HZX], p), ldg<V>(a.co[C0 + HZX], p), dHzx);
-                const V nzy = upd(ozy, ldg<V>(a.co[T0 + HZY], p), ldg<V>(a.co[C0 + HZY], p), dHzy);
-                hn.x = cadd(nxy, nxz);
-                hn.y = cadd(nyx, nyz);
-                hn.z = cadd(nzx, nzy);
+                const Z dHxy = A::sub(e0.y, ezm.y);   // +dz Ey
+                const Z dHxz = A::sub(eym.z, e0.z);   // -dy Ez
+                const Z dHyx = A::sub(ezm.x, e0.x);   // -dz Ex
+                const Z dHyz = A::sub(e0.z, exm.z);   // +dx Ez
+                const Z dHzx = A::sub(e0.x, eym.x);   // +dy Ex
+                const Z dHzy = A::sub(exm.y, e0.y);   // -dx Ey
+                const Z oxy = A::ld_field(a.src[HXY], p), oxz = A::ld_field(a.src[HXZ], p);
+                const Z oyx = A::ld_field(a.src[HYX], p), oyz = A::ld_field(a.src[HYZ], p);
+                const Z ozx = A::ld_field(a.src[HZX], p), ozy = A::ld_field(a.src[HZY], p);
+                const Z nxy = A::upd_src(oxy, A::ld_coef(a.co[T0 + HXY], p), A::ld_coef(a.co[C0 + HXY], p), dHxy, A::ld_coef(a.co[SRC_HXY], p));
+                const Z nxz = A::upd(oxz, A::ld_coef(a.co[T0 + HXZ], p), A::ld_coef(a.co[C0 + HXZ], p), dHxz);
+                const Z nyx = A::upd_src(oyx, A::ld_coef(a.co[T0 + HYX], p), A::ld_coef(a.co[C0 + HYX], p), dHyx, A::ld_coef(a.co[SRC_HYX], p));
+                const Z nyz = A::upd(oyz, A::ld_coef(a.co[T0 + HYZ], p), A::ld_coef(a.co[C0 + HYZ], p), dHyz);
+                const Z nzx = A::upd(ozx, A::ld_coef(a.co[T0 + HZX], p), A::ld_coef(a.co[C0 + HZX], p), dHzx);
+                const Z nzy = A::upd(ozy, A::ld_coef(a.co[T0 + HZY], p), A::ld_coef(a.co[C0 + HZY], p), dHzy);
+                hn.x = A::add(nxy, nxz);
+                hn.y = A::add(nyx, nyz);
+                hn.z = A::add(nzx, nzy);
                 if (hx < nix && hy < niy && k < z1) {
-                    stg(a.dst[HXY], p, nxy); stg(a.dst[HXZ], p, nxz);
-                    stg(a.dst[HYX], p, nyx); stg(a.dst[HYZ], p, nyz);
-                    stg(a.dst[HZX], p, nzx); stg(a.dst[HZY], p, nzy);
+                    A::st_field(a.dst[HXY], p, nxy); A::st_field(a.dst[HXZ], p, nxz);
+                    A::st_field(a.dst[HYX], p, nyx); A::st_field(a.dst[HYZ], p, nyz);
+                    A::st_field(a.dst[HZX], p, nzx); A::st_field(a.dst[HZY], p, nzy);
                     if (want_norm) {
-                        const V dx = csub(hn.x, cadd(oxy, oxz));
-                        const V dy = csub(hn.y, cadd(oyx, oyz));
-                        const V dz = csub(hn.z, cadd(ozx, ozy));
-                        acc_d += (double)dx.x * dx.x + (double)dx.y * dx.y + (double)dy.x * dy.x +
-                                 (double)dy.y * dy.y + (double)dz.x * dz.x + (double)dz.y * dz.y;
-                        acc_x += (double)hn.x.x * hn.x.x + (double)hn.x.y * hn.x.y + (double)hn.y.x * hn.y.x +
-                                 (double)hn.y.y * hn.y.y + (double)hn.z.x * hn.z.x + (double)hn.z.y * hn.z.y;
+                        acc_d += dnorm2<A>(hn.x, A::add(oxy, oxz)) + dnorm2<A>(hn.y, A::add(oyx, oyz)) +
+                                 dnorm2<A>(hn.z, A::add(ozx, ozy));
+                        acc_x += norm2<A>(hn.x) + norm2<A>(hn.y) + norm2<A>(hn.z);
                     }
                 }
             }
@@ -194,38 +172,34 @@ sweep_kernel(const SweepArgs a) {
                 const int ex = w % nix, ey = w / nix;
                 const int gx = i0 + ex, gy = j0 + ey;
                 const size_t p = (size_t)ke * plane + (size_t)gy * nx + gx;
-                const Vec3<V> h0 = sH[prev][ey][ex];
-                const Vec3<V> hxp = sH[prev][ey][ex + 1];
-                const Vec3<V> hyp = sH[prev][ey + 1][ex];
-                const Vec3<V> hzp = sH[cur][ey][ex];
+                const Vec3<Z> h0 = sH[prev][ey][ex];
+                const Vec3<Z> hxp = sH[prev][ey][ex + 1];
+                const Vec3<Z> hyp = sH[prev][ey + 1][ex];
+                const Vec3<Z> hzp = sH[cur][ey][ex];
                 // forward differences with the curl sign folded in
-                const V dExy = csub(h0.y, hzp.y);   // -dz Hy
-                const V dExz = csub(hyp.z, h0.z);   // +dy Hz
-                const V dEyx = csub(hzp.x, h0.x);   // +dz Hx
-                const V dEyz = csub(h0.z, hxp.z);   // -dx Hz
-                const V dEzx = csub(h0.x, hyp.x);   // -dy Hx
-                const V dEzy = csub(hxp.y, h0.y);   // +dx Hy
-                const V oxy = ldg<V>(a.src[EXY], p), oxz = ldg<V>(a.src[EXZ], p);
-                const V oyx = ldg<V>(a.src[EYX], p), oyz = ldg<V>(a.src[EYZ], p);
-                const V ozx = ldg<V>(a.src[EZX], p), ozy = ldg<V>(a.src[EZY], p);
-                const V nxy = upd_src(oxy, ldg<V>(a.co[T0 + EXY], p), ldg<V>(a.co[C0 + EXY], p), dExy, ldg<V>(a.co[SRC_EXY], p));
-                const V nxz = upd(oxz, ldg<V>(a.co[T0 + EXZ], p), ldg<V>(a.co[C0 + EXZ], p), dExz);
-                const V nyx = upd_src(oyx, ldg<V>(a.co[T0 + EYX], p), ldg<V>(a.co[C0 + EYX], p), dEyx, ldg<V>(a.co[SRC_EYX], p));
-                const V nyz = upd(oyz, ldg<V>(a.co[T0 + EYZ], p), ldg<V>(a.co[C0 + EYZ], p), dEyz);
-                const V nzx = upd(ozx, ldg<V>(a.co[T0 + EZX], p), ldg<V>(a.co[C0 + EZX], p), dEzx);
-                const V nzy = upd(ozy, ldg<V>(a.co[T0 + EZY], p), ldg<V>(a.co[C0 + EZY], p), dEzy);
-                stg(a.dst[EXY], p, nxy); stg(a.dst[EXZ], p, nxz);
-                stg(a.dst[EYX], p, nyx); stg(a.dst[EYZ], p, nyz);
-                stg(a.dst[EZX], p, nzx); stg(a.dst[EZY], p, nzy);
+                const Z dExy = A::sub(h0.y, hzp.y);   // -dz Hy
+                const Z dExz = A::sub(hyp.z, h0.z);   // +dy Hz
+                const Z dEyx = A::sub(hzp.x, h0.x);   // +dz Hx
+                const Z dEyz = A::sub(h0.z, hxp.z);   // -dx Hz
+                const Z dEzx = A::sub(h0.x, hyp.x);   // -dy Hx
+                const Z dEzy = A::sub(hxp.y, h0.y);   // +dx Hy
+                const Z oxy = A::ld_field(a.src[EXY], p), oxz = A::ld_field(a.src[EXZ], p);
+                const Z oyx = A::ld_field(a.src[EYX], p), oyz = A::ld_field(a.src[EYZ], p);
+                const Z ozx = A::ld_field(a.src[EZX], p), ozy = A::ld_field(a.src[EZY], p);
+                const Z nxy = A::upd_src(oxy, A::ld_coef(a.co[T0 + EXY], p), A::ld_coef(a.co[C0 + EXY], p), dExy, A::ld_coef(a.co[SRC_EXY], p));
+                const Z nxz = A::upd(oxz, A::ld_coef(a.co[T0 + EXZ], p), A::ld_coef(a.co[C0 + EXZ], p), dExz);
+                const Z nyx = A::upd_src(oyx, A::ld_coef(a.co[T0 + EYX], p), A::ld_coef(a.co[C0 + EYX], p), dEyx, A::ld_coef(a.co[SRC_EYX], p));
+                const Z nyz = A::upd(oyz, A::ld_coef(a.co[T0 + EYZ], p), A::ld_coef(a.co[C0 + EYZ], p), dEyz);
+                const Z nzx = A::upd(ozx, A::ld_coef(a.co[T0 + EZX], p), A::ld_coef(a.co[C0 + EZX], p), dEzx);
+                const Z nzy = A::upd(ozy, A::ld_coef(a.co[T0 + EZY], p), A::ld_coef(a.co[C0 + EZY], p), dEzy);
+                A::st_field(a.dst[EXY], p, nxy); A::st_field(a.dst[EXZ], p, nxz);
+                A::st_field(a.dst[EYX], p, nyx); A::st_field(a.dst[EYZ], p, nyz);
+                A::st_field(a.dst[EZX], p, nzx); A::st_field(a.dst[EZY], p, nzy);
                 if (want_norm) {
-                    const V fx = cadd(nxy, nxz), fy = cadd(nyx, nyz), fz = cadd(nzx, nzy);
-                    const V dx = csub(fx, cadd(oxy, oxz));
-                    const V dy = csub(fy, cadd(oyx, oyz));
-                    const V dz = csub(fz, cadd(ozx, ozy));
-                    acc_d += (double)dx.x * dx.x + (double)dx.y * dx.y + (double)dy.x * dy.x +
-                             (double)dy.y * dy.y + (double)dz.x * dz.x + (double)dz.y * dz.y;
-                    acc_x += (double)fx.x * fx.x + (double)fx.y * fx.y + (double)fy.x * fy.x +
-                             (double)fy.y * fy.y + (double)fz.x * fz.x + (double)fz.y * fz.y;
+                    const Z fx = A::add(nxy, nxz), fy = A::add(nyx, nyz), fz = A::add(nzx, nzy);
+                    acc_d += dnorm2<A>(fx, A::add(oxy, oxz)) + dnorm2<A>(fy, A::add(oyx, oyz)) +
+                             dnorm2<A>(fz, A::add(ozx, ozy));
+                    acc_x += norm2<A>(fx) + norm2<A>(fy) + norm2<A>(fz);
                 }
             }
         }

@@ -14,6 +14,7 @@ from . import build as _build
 
 THIIM_C128 = 0
 THIIM_C64 = 1
+THIIM_C128_PAIR = 2
 THIIM_PERIODIC_X = 1
 THIIM_PERIODIC_Y = 2
 THIIM_PERIODIC_Z = 4
@@ -193,7 +194,7 @@ class Solver:
         import torch
         self.nx, self.ny, self.nz = nx, ny, nz
         self.precision = precision
-        self.dtype = torch.complex128 if precision == THIIM_C128 else torch.complex64
+        self.dtype = torch.complex64 if precision == THIIM_C64 else torch.complex128
         self.device = torch.device(device or "cuda")
         self.ctx = thiim_create(nx, ny, nz, precision, bc, stream)
         self.fields = None

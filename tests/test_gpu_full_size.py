@@ -1,7 +1,8 @@
 """Full-size (512^3) parity on sampled cells, in the launch configuration the
 benchmark times (the library's default tiling for this grid).
 
-The GPU runs 3 iterations of the 512^3 stack (coefficients built on the
+The GPU runs 3 iterations of the 512^3 stack (native FP64 and FP32-pair
+arithmetic; 3 iterations run all three pair-format kernels) (coefficients built on the
 device from the permittivity map) from seeded random fields.  A cell's value
 after n iterations depends only on inputs within n cells of it, so the oracle
 recomputes each sampled cell on a 9^3 block around it (radius 4 > 3; periodic
@@ -34,7 +35,8 @@ def _samples(n):
     return out
 
 
-def test_stack512_sampled_cells_match_oracle():
+@pytest.mark.parametrize("precision", [0, 2])
+def test_stack512_sampled_cells_match_oracle(precision):
     import torch
     import paper_1510_05218_gb300 as p
     st = stack_config("stack512")
@@ -42,7 +44,7 @@ def test_stack512_sampled_cells_match_oracle():
     shape = (n, n, n)
     eps_host = st.eps()
     eps = torch.from_numpy(eps_host).to("cuda")
-    ctx = p.thiim_create(n, n, n, p.THIIM_C128, 3)
+    ctx = p.thiim_create(n, n, n, precision, 3)
     try:
         co = [torch.empty(shape, dtype=torch.complex128, device="cuda") for _ in range(28)]
         p.thiim_build_coeffs(ctx, eps, st.sigma_pml_e(), st.sigma_pml_h(), st.omega, st.tau, st.k_s, 1.0, co)
