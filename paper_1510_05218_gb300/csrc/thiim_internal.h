@@ -8,10 +8,21 @@
 
 namespace thiim {
 
-// Sweep tile: TX x TY cells per CTA, NT threads.
+// Sweep tile: TX x TY cells per CTA, NT threads, MINB resident CTAs per SM
+// requested from the register allocator (0 = no request).
+#ifndef THIIM_SWEEP_TY
+#define THIIM_SWEEP_TY 8
+#endif
+#ifndef THIIM_SWEEP_NT
+#define THIIM_SWEEP_NT 256
+#endif
+#ifndef THIIM_SWEEP_MINB
+#define THIIM_SWEEP_MINB 0
+#endif
 constexpr int SWEEP_TX = 32;
-constexpr int SWEEP_TY = 8;
-constexpr int SWEEP_NT = 256;
+constexpr int SWEEP_TY = THIIM_SWEEP_TY;
+constexpr int SWEEP_NT = THIIM_SWEEP_NT;
+constexpr int SWEEP_MINB = THIIM_SWEEP_MINB;
 
 // Enqueue one fused iteration; grid = (tiles_x * tiles_y, chunks).
 cudaError_t launch_sweep_f64(const SweepArgs &a, dim3 grid, cudaStream_t s);

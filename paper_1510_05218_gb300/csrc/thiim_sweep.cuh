@@ -64,8 +64,8 @@ __device__ __forceinline__ double dnorm2(typename A::Z a, typename A::Z b) {
     return x * x + y * y;
 }
 
-template <typename A, int TX, int TY, int NT>
-__global__ void __launch_bounds__(NT)
+template <typename A, int TX, int TY, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB)
 sweep_kernel(const SweepArgs a) {
     typedef typename A::Z Z;
     constexpr int EW = TX + 2, EH = TY + 2;   // E^n region: -1 .. TX (x), -1 .. TY (y)

@@ -4,7 +4,7 @@
 namespace thiim {
 
 cudaError_t launch_sweep_f32(const SweepArgs &a, dim3 grid, cudaStream_t s) {
-    sweep_kernel<Native<float>, SWEEP_TX, SWEEP_TY, SWEEP_NT><<<grid, SWEEP_NT, 0, s>>>(a);
+    sweep_kernel<Native<float>, SWEEP_TX, SWEEP_TY, SWEEP_NT, SWEEP_MINB><<<grid, SWEEP_NT, 0, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -33,7 +33,7 @@ class ThiimError(RuntimeError):
 
 
 def lib_path() -> str:
-    return _build.LIB
+    return os.environ.get("THIIM_LIBRARY") or _build.LIB
 
 
 def load_library(build_if_missing: bool = False):
@@ -41,7 +41,7 @@ def load_library(build_if_missing: bool = False):
     global _lib
     if _lib is not None:
         return _lib
-    path = _build.LIB
+    path = lib_path()
     if not os.path.exists(path):
         if not build_if_missing:
             raise RuntimeError("libthiim.so is not built (%s); run __graft_entry__.build() or "
