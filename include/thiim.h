@@ -172,6 +172,32 @@ int thiim_build_coeffs(thiim_ctx *ctx, const void *eps_r,
                        double amp_im, void *const coeff[THIIM_N_COEFFS]);
 
 /*
+ * thiim_mixed_solve — complex64 sweeps with FP64 defect correction.
+ *   ctx:        a THIIM_C64 context with its complex64 coefficients set
+ *               (thiim_set_coeffs / thiim_build_coeffs) and 12 complex64
+ *               work arrays given to thiim_set_fields (they receive the
+ *               corrections; their contents are overwritten).
+ *   coeff64:    the same problem's 28 complex128 coefficient arrays.
+ *   x64:        12 complex128 field arrays: the FP64 iterate, updated in place.
+ *   Each outer step evaluates the FP64 defect r = F(x) - x (one FP64 sweep
+ *   with coeff64; the relative full-field norm ||r|| / ||F(x)|| is the
+ *   residual of thiim_residual), stops if it is <= tol, otherwise advances
+ *   the correction inner_iters times by delta <- M32 delta + r (complex64,
+ *   FP32 arithmetic, delta starting at 0) and sets x += delta.  In exact
+ *   arithmetic one outer step equals inner_iters plain iterations.  At most
+ *   max_outer corrections are applied; the defect is evaluated once more
+ *   after the last one.  Synchronises the stream once per outer step.
+ *   *outer_done: corrections applied; *rel_residual: last defect residual.
+ *   Allocates 12 complex64 arrays for r on the first call.
+ * Errors: THIIM_ERR_ARG (not a THIIM_C64 context, inner_iters < 1, NULL),
+ * THIIM_ERR_STATE, THIIM_ERR_ALIGN, THIIM_ERR_NOMEM, THIIM_ERR_NONFINITE,
+ * THIIM_ERR_CUDA.
+ */
+int thiim_mixed_solve(thiim_ctx *ctx, void *const coeff64[THIIM_N_COEFFS],
+                      void *const x64[THIIM_N_FIELDS], int inner_iters, int max_outer,
+                      double tol, int *outer_done, double *rel_residual);
+
+/*
  * thiim_step_noalloc — one THIIM iteration that allocates no memory.
  *   For callers that cannot call cudaMalloc (code running under another
  *   framework's memory pool or allocator hooks, or with all device memory

@@ -9,36 +9,11 @@
 #include <new>
 
 #include "../../include/thiim.h"
-#include "thiim_internal.h"
+#include "thiim_ctx.h"
 
 using namespace thiim;
 
-struct thiim_ctx {
-    int nx, ny, nz;
-    int precision;
-    unsigned bc;
-    cudaStream_t stream;
-    int device;
-    int num_sms;
-    size_t elem;                 // bytes per complex element
-    size_t n_cells;
-    void *coeff[THIIM_N_COEFFS];
-    void *user[THIIM_N_FIELDS];  // caller's field arrays (hold x^n between calls)
-    void *alt[THIIM_N_FIELDS];   // library's second field set
-    void *pair_co[THIIM_N_COEFFS];  // THIIM_C128_PAIR: coefficients split into float4 pairs
-    bool pair_dirty;             // coefficients changed since they were last split
-    bool have_coeffs, have_fields, have_norm;
-    int zchunk;                  // planes per CTA of the sweep
-    double *partials;            // 2 doubles per sweep CTA
-    size_t partials_cap;         // in CTAs
-    double *norms;               // device: |dF|^2, |F|^2 of the last iteration
-    double *pml;                 // device: 2*nz absorbing-layer conductivities
-    int *flag;                   // device: error flag of the coefficient builder
-};
-
-namespace {
-
-int cuda_status(cudaError_t e) { return e == cudaSuccess ? THIIM_OK : THIIM_ERR_CUDA; }
+namespace thiim {
 
 bool aligned(const void *p, size_t a) { return ((uintptr_t)p % a) == 0; }
 
@@ -69,7 +44,7 @@ int ensure_partials(thiim_ctx *c, size_t ctas) {
 }
 
 // Sum the per-CTA partial pairs in a fixed order (deterministic).
-__global__ void finalize_norms(const double *partials, size_t n, double *out) {
+__global__ void finalize_norms_kernel(const double *partials, size_t n, double *out) {
     __shared__ double sd[256], sx[256];
     double d = 0.0, x = 0.0;
     for (size_t i = threadIdx.x; i < n; i += blockDim.x) {
@@ -88,6 +63,15 @@ __global__ void finalize_norms(const double *partials, size_t n, double *out) {
     }
     if (threadIdx.x == 0) { out[0] = sd[0]; out[1] = sx[0]; }
 }
+
+cudaError_t finalize_norms(const double *partials, size_t n, double *out, cudaStream_t s) {
+    finalize_norms_kernel<<<1, 256, 0, s>>>(partials, n, out);
+    return cudaGetLastError();
+}
+
+}  // namespace thiim
+
+namespace {
 
 // ---- coefficient builder (Eqs. 3-5 solved for the new value) ---------------
 
@@ -319,8 +303,7 @@ int thiim_iterate(thiim_ctx *c, int n_iters) {
                 return THIIM_ERR_CUDA;
         }
     }
-    finalize_norms<<<1, 256, 0, c->stream>>>(c->partials, ctas, c->norms);
-    if (cudaGetLastError() != cudaSuccess) return THIIM_ERR_CUDA;
+    if (finalize_norms(c->partials, ctas, c->norms, c->stream) != cudaSuccess) return THIIM_ERR_CUDA;
     c->have_norm = true;
     return THIIM_OK;
 }
@@ -412,6 +395,8 @@ void thiim_destroy(thiim_ctx *c) {
         if (c->alt[i]) cudaFree(c->alt[i]);
     for (int i = 0; i < THIIM_N_COEFFS; ++i)
         if (c->pair_co[i]) cudaFree(c->pair_co[i]);
+    for (int i = 0; i < THIIM_N_FIELDS; ++i)
+        if (c->mix_r[i]) cudaFree(c->mix_r[i]);
     if (c->partials) cudaFree(c->partials);
     if (c->norms) cudaFree(c->norms);
     if (c->pml) cudaFree(c->pml);

@@ -1,0 +1,47 @@
+// The library context and helpers shared by the C-ABI translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "../../include/thiim.h"
+#include "thiim_internal.h"
+
+struct thiim_ctx {
+    int nx, ny, nz;
+    int precision;
+    unsigned bc;
+    cudaStream_t stream;
+    int device;
+    int num_sms;
+    size_t elem;                 // bytes per complex element
+    size_t n_cells;
+    void *coeff[THIIM_N_COEFFS];
+    void *user[THIIM_N_FIELDS];  // caller's field arrays (hold x^n between calls)
+    void *alt[THIIM_N_FIELDS];   // library's second field set
+    void *pair_co[THIIM_N_COEFFS];  // THIIM_C128_PAIR: coefficients split into float4 pairs
+    bool pair_dirty;             // coefficients changed since they were last split
+    bool have_coeffs, have_fields, have_norm;
+    int zchunk;                  // planes per CTA of the sweep
+    double *partials;            // 2 doubles per sweep CTA
+    size_t partials_cap;         // in CTAs
+    double *norms;               // device: |dF|^2, |F|^2 of the last iteration
+    double *pml;                 // device: 2*nz absorbing-layer conductivities
+    int *flag;                   // device: error flag of the coefficient builder
+    // defect-correction state (thiim_mixed_solve)
+    void *mix_r[THIIM_N_FIELDS]; // complex64 defect r = F64(x) - x
+};
+
+
+namespace thiim {
+
+bool aligned(const void *p, size_t a);
+int tiles_x(const thiim_ctx *c);
+int tiles_y(const thiim_ctx *c);
+int default_zchunk(const thiim_ctx *c);
+int ensure_partials(thiim_ctx *c, size_t ctas);
+// Sum n per-CTA partial pairs in a fixed order into out[0], out[1].
+cudaError_t finalize_norms(const double *partials, size_t n, double *out, cudaStream_t s);
+
+}  // namespace thiim

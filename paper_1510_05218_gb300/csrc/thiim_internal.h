@@ -32,6 +32,11 @@ cudaError_t launch_sweep_f32(const SweepArgs &a, dim3 grid, cudaStream_t s);
 // float4 pairs (see split_coeffs).
 cudaError_t launch_sweep_pair(const SweepArgs &a, dim3 grid, cudaStream_t s, bool in_pairs, bool out_pairs);
 
+// Defect-correction sweeps: FP64 defect r = F(x) - x written as complex64,
+// and the complex64 correction iteration delta <- M delta + r (a.xsrc = r).
+cudaError_t launch_defect_f64(const SweepArgs &a, dim3 grid, cudaStream_t s);
+cudaError_t launch_correct_f32(const SweepArgs &a, dim3 grid, cudaStream_t s);
+
 // Split n complex128 values of each of `count` arrays into float4 pairs.
 cudaError_t split_coeffs(const void *const *src, void *const *dst, int count, size_t n, cudaStream_t s);
 

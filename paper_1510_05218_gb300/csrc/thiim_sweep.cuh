@@ -41,7 +41,27 @@ struct SweepArgs {
     int zchunk;            // planes per CTA
     int tiles_x;           // CTAs along x
     double *partials;      // 2 doubles per CTA (|dF|^2, |F|^2) or nullptr
+    const void *xsrc[12];  // SWEEP_CORRECT: per-split source arrays replacing Src
 };
+
+// Sweep modes.
+//   SWEEP_PLAIN    dst <- one iteration of src.
+//   SWEEP_DEFECT   dst <- (one iteration of src) - src, stored as complex64:
+//                  the defect r = F(x) - x of the defect-correction restart.
+//                  Where the two splits of a component have bit-identical t
+//                  and c (everywhere outside the absorbing layers) their
+//                  difference is an undamped mode that no full field sees;
+//                  the pair's defect is stored balanced, (r_a + r_b)/2 each,
+//                  which keeps the full-field defect r_a + r_b and keeps the
+//                  complex64 correction from carrying that large, never
+//                  decaying part (whose FP32 cancellation would otherwise
+//                  set a floor under the FP64 residual).
+//   SWEEP_CORRECT  dst <- M src + xsrc: the correction iteration
+//                  delta <- M delta + r, where M is the linear part of one
+//                  iteration (no Src).  r is added to what is stored only; the
+//                  E update reads the new H *without* r_H, otherwise the H
+//                  defect would leak into E through the curl a second time.
+enum { SWEEP_PLAIN = 0, SWEEP_DEFECT = 1, SWEEP_CORRECT = 2 };
 
 template <typename Z> struct Vec3 { Z x, y, z; };
 
@@ -64,10 +84,52 @@ __device__ __forceinline__ double dnorm2(typename A::Z a, typename A::Z b) {
     return x * x + y * y;
 }
 
-template <typename A, int TX, int TY, int NT, int MINB>
+template <typename A, int MODE>
+struct SplitIO {
+    typedef typename A::Z Z;
+    // t x + c d (+ Src if the split has a source array; none in SWEEP_CORRECT).
+    // The result feeds the full-field sums that the E update reads.
+    __device__ static __forceinline__ Z update(const SweepArgs &a, int s, int src_coef, size_t p, Z x, Z d) {
+        const Z t = A::ld_coef(a.co[T0 + s], p), c = A::ld_coef(a.co[C0 + s], p);
+        if (MODE != SWEEP_CORRECT && src_coef >= 0) return A::upd_src(x, t, c, d, A::ld_coef(a.co[src_coef], p));
+        return A::upd(x, t, c, d);
+    }
+    // Store splits s and s+1 (the two parts of one component).
+    __device__ static __forceinline__ void store_pair(const SweepArgs &a, int s, size_t p, Z va, Z olda, Z vb, Z oldb) {
+        if (MODE == SWEEP_DEFECT) {
+            double ar = A::re(va) - A::re(olda), ai = A::im(va) - A::im(olda);
+            double br = A::re(vb) - A::re(oldb), bi = A::im(vb) - A::im(oldb);
+            const Z ta = A::ld_coef(a.co[T0 + s], p), tb = A::ld_coef(a.co[T0 + s + 1], p);
+            const Z ca = A::ld_coef(a.co[C0 + s], p), cb = A::ld_coef(a.co[C0 + s + 1], p);
+            if (A::re(ta) == A::re(tb) && A::im(ta) == A::im(tb) && A::re(ca) == A::re(cb) && A::im(ca) == A::im(cb)) {
+                ar = br = 0.5 * (ar + br);
+                ai = bi = 0.5 * (ai + bi);
+            }
+            stg_as<float2>(a.dst[s], p, make_float2((float)ar, (float)ai));
+            stg_as<float2>(a.dst[s + 1], p, make_float2((float)br, (float)bi));
+        } else {
+            store(a, s, p, va, olda);
+            store(a, s + 1, p, vb, oldb);
+        }
+    }
+    // Store the new value of split s (plus xsrc[s] in SWEEP_CORRECT; minus
+    // the old value, as complex64, in SWEEP_DEFECT).
+    __device__ static __forceinline__ void store(const SweepArgs &a, int s, size_t p, Z v, Z old) {
+        if (MODE == SWEEP_CORRECT) {
+            A::st_field(a.dst[s], p, A::add(v, A::ld_coef(a.xsrc[s], p)));
+        } else if (MODE == SWEEP_DEFECT) {
+            stg_as<float2>(a.dst[s], p, make_float2((float)(A::re(v) - A::re(old)), (float)(A::im(v) - A::im(old))));
+        } else {
+            A::st_field(a.dst[s], p, v);
+        }
+    }
+};
+
+template <typename A, int TX, int TY, int NT, int MINB, int MODE = SWEEP_PLAIN>
 __global__ void __launch_bounds__(NT, MINB)
 sweep_kernel(const SweepArgs a) {
     typedef typename A::Z Z;
+    typedef SplitIO<A, MODE> IO;
     constexpr int EW = TX + 2, EH = TY + 2;   // E^n region: -1 .. TX (x), -1 .. TY (y)
     constexpr int HW = TX + 1, HH = TY + 1;   // new-H region: 0 .. TX, 0 .. TY
     __shared__ Vec3<Z> sE[2][EH][EW];         // full E^n at planes k (cur) and k-1
@@ -141,19 +203,19 @@ sweep_kernel(const SweepArgs a) {
                 const Z oxy = A::ld_field(a.src[HXY], p), oxz = A::ld_field(a.src[HXZ], p);
                 const Z oyx = A::ld_field(a.src[HYX], p), oyz = A::ld_field(a.src[HYZ], p);
                 const Z ozx = A::ld_field(a.src[HZX], p), ozy = A::ld_field(a.src[HZY], p);
-                const Z nxy = A::upd_src(oxy, A::ld_coef(a.co[T0 + HXY], p), A::ld_coef(a.co[C0 + HXY], p), dHxy, A::ld_coef(a.co[SRC_HXY], p));
-                const Z nxz = A::upd(oxz, A::ld_coef(a.co[T0 + HXZ], p), A::ld_coef(a.co[C0 + HXZ], p), dHxz);
-                const Z nyx = A::upd_src(oyx, A::ld_coef(a.co[T0 + HYX], p), A::ld_coef(a.co[C0 + HYX], p), dHyx, A::ld_coef(a.co[SRC_HYX], p));
-                const Z nyz = A::upd(oyz, A::ld_coef(a.co[T0 + HYZ], p), A::ld_coef(a.co[C0 + HYZ], p), dHyz);
-                const Z nzx = A::upd(ozx, A::ld_coef(a.co[T0 + HZX], p), A::ld_coef(a.co[C0 + HZX], p), dHzx);
-                const Z nzy = A::upd(ozy, A::ld_coef(a.co[T0 + HZY], p), A::ld_coef(a.co[C0 + HZY], p), dHzy);
+                const Z nxy = IO::update(a, HXY, SRC_HXY, p, oxy, dHxy);
+                const Z nxz = IO::update(a, HXZ, -1, p, oxz, dHxz);
+                const Z nyx = IO::update(a, HYX, SRC_HYX, p, oyx, dHyx);
+                const Z nyz = IO::update(a, HYZ, -1, p, oyz, dHyz);
+                const Z nzx = IO::update(a, HZX, -1, p, ozx, dHzx);
+                const Z nzy = IO::update(a, HZY, -1, p, ozy, dHzy);
                 hn.x = A::add(nxy, nxz);
                 hn.y = A::add(nyx, nyz);
                 hn.z = A::add(nzx, nzy);
                 if (hx < nix && hy < niy && k < z1) {
-                    A::st_field(a.dst[HXY], p, nxy); A::st_field(a.dst[HXZ], p, nxz);
-                    A::st_field(a.dst[HYX], p, nyx); A::st_field(a.dst[HYZ], p, nyz);
-                    A::st_field(a.dst[HZX], p, nzx); A::st_field(a.dst[HZY], p, nzy);
+                    IO::store_pair(a, HXY, p, nxy, oxy, nxz, oxz);
+                    IO::store_pair(a, HYX, p, nyx, oyx, nyz, oyz);
+                    IO::store_pair(a, HZX, p, nzx, ozx, nzy, ozy);
                     if (want_norm) {
                         acc_d += dnorm2<A>(hn.x, A::add(oxy, oxz)) + dnorm2<A>(hn.y, A::add(oyx, oyz)) +
                                  dnorm2<A>(hn.z, A::add(ozx, ozy));
@@ -186,15 +248,15 @@ sweep_kernel(const SweepArgs a) {
                 const Z oxy = A::ld_field(a.src[EXY], p), oxz = A::ld_field(a.src[EXZ], p);
                 const Z oyx = A::ld_field(a.src[EYX], p), oyz = A::ld_field(a.src[EYZ], p);
                 const Z ozx = A::ld_field(a.src[EZX], p), ozy = A::ld_field(a.src[EZY], p);
-                const Z nxy = A::upd_src(oxy, A::ld_coef(a.co[T0 + EXY], p), A::ld_coef(a.co[C0 + EXY], p), dExy, A::ld_coef(a.co[SRC_EXY], p));
-                const Z nxz = A::upd(oxz, A::ld_coef(a.co[T0 + EXZ], p), A::ld_coef(a.co[C0 + EXZ], p), dExz);
-                const Z nyx = A::upd_src(oyx, A::ld_coef(a.co[T0 + EYX], p), A::ld_coef(a.co[C0 + EYX], p), dEyx, A::ld_coef(a.co[SRC_EYX], p));
-                const Z nyz = A::upd(oyz, A::ld_coef(a.co[T0 + EYZ], p), A::ld_coef(a.co[C0 + EYZ], p), dEyz);
-                const Z nzx = A::upd(ozx, A::ld_coef(a.co[T0 + EZX], p), A::ld_coef(a.co[C0 + EZX], p), dEzx);
-                const Z nzy = A::upd(ozy, A::ld_coef(a.co[T0 + EZY], p), A::ld_coef(a.co[C0 + EZY], p), dEzy);
-                A::st_field(a.dst[EXY], p, nxy); A::st_field(a.dst[EXZ], p, nxz);
-                A::st_field(a.dst[EYX], p, nyx); A::st_field(a.dst[EYZ], p, nyz);
-                A::st_field(a.dst[EZX], p, nzx); A::st_field(a.dst[EZY], p, nzy);
+                const Z nxy = IO::update(a, EXY, SRC_EXY, p, oxy, dExy);
+                const Z nxz = IO::update(a, EXZ, -1, p, oxz, dExz);
+                const Z nyx = IO::update(a, EYX, SRC_EYX, p, oyx, dEyx);
+                const Z nyz = IO::update(a, EYZ, -1, p, oyz, dEyz);
+                const Z nzx = IO::update(a, EZX, -1, p, ozx, dEzx);
+                const Z nzy = IO::update(a, EZY, -1, p, ozy, dEzy);
+                IO::store_pair(a, EXY, p, nxy, oxy, nxz, oxz);
+                IO::store_pair(a, EYX, p, nyx, oyx, nyz, oyz);
+                IO::store_pair(a, EZX, p, nzx, ozx, nzy, ozy);
                 if (want_norm) {
                     const Z fx = A::add(nxy, nxz), fy = A::add(nyx, nyz), fz = A::add(nzx, nzy);
                     acc_d += dnorm2<A>(fx, A::add(oxy, oxz)) + dnorm2<A>(fy, A::add(oyx, oyz)) +

@@ -8,4 +8,9 @@ cudaError_t launch_sweep_f32(const SweepArgs &a, dim3 grid, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+cudaError_t launch_correct_f32(const SweepArgs &a, dim3 grid, cudaStream_t s) {
+    sweep_kernel<Native<float>, SWEEP_TX, SWEEP_TY, SWEEP_NT, SWEEP_MINB, SWEEP_CORRECT><<<grid, SWEEP_NT, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
 }  // namespace thiim

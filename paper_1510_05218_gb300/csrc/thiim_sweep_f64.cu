@@ -8,4 +8,9 @@ cudaError_t launch_sweep_f64(const SweepArgs &a, dim3 grid, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+cudaError_t launch_defect_f64(const SweepArgs &a, dim3 grid, cudaStream_t s) {
+    sweep_kernel<Native<double>, SWEEP_TX, SWEEP_TY, SWEEP_NT, SWEEP_MINB, SWEEP_DEFECT><<<grid, SWEEP_NT, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
 }  // namespace thiim

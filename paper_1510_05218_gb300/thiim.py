@@ -63,6 +63,9 @@ def load_library(build_if_missing: bool = False):
     lib.thiim_step_noalloc.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_uint,
                                        P12, P12, P28, vp, ctypes.POINTER(ctypes.c_double)]
     lib.thiim_step_noalloc.restype = ctypes.c_int
+    lib.thiim_mixed_solve.argtypes = [vp, P28, P12, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                      ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
+    lib.thiim_mixed_solve.restype = ctypes.c_int
     lib.thiim_destroy.argtypes = [vp]
     lib.thiim_destroy.restype = None
     lib.thiim_strerror.argtypes = [ctypes.c_int]
@@ -156,6 +159,16 @@ def thiim_build_coeffs(ctx, eps_r, sigma_pml_e, sigma_pml_h, omega, tau, k_s, am
         None if se is None else se.ctypes.data_as(ctypes.c_void_p),
         None if sh is None else sh.ctypes.data_as(ctypes.c_void_p),
         float(omega), float(tau), int(k_s), amp.real, amp.imag, _ptrs(coeffs, 28, "coefficient")))
+
+
+def thiim_mixed_solve(ctx, coeffs64, x64, inner_iters=50, max_outer=1, tol=0.0):
+    """Defect-correction solve; returns (corrections applied, last FP64 residual)."""
+    done = ctypes.c_int()
+    r = ctypes.c_double()
+    _check("thiim_mixed_solve", load_library().thiim_mixed_solve(
+        ctx, _ptrs(coeffs64, 28, "coefficient"), _ptrs(x64, 12, "field"), int(inner_iters), int(max_outer),
+        float(tol), ctypes.byref(done), ctypes.byref(r)))
+    return done.value, r.value
 
 
 def thiim_step_noalloc(nx, ny, nz, precision, bc_flags, src, dst, coeffs, stream=None, want_residual=True):
