@@ -198,6 +198,27 @@ int thiim_mixed_solve(thiim_ctx *ctx, void *const coeff64[THIIM_N_COEFFS],
                       double tol, int *outer_done, double *rel_residual);
 
 /*
+ * thiim_batch_iterate — advance nb independent solves together.
+ *   ctx[0..nb-1]: contexts of one precision on one device, each with fields
+ *                 and coefficients set; grids may differ in size.
+ *   Every iteration of all still-active solves is ONE persistent launch that
+ *   walks a list of (solve, 32x8 column, z chunk) items; check_every
+ *   iterations (even, >= 2) and the per-solve residual run as one captured
+ *   CUDA graph, after which solves whose residual (as thiim_residual) is
+ *   <= tol, or which reached max_iters, leave the batch.
+ *   All work runs on ctx[0]'s stream; the call synchronises it after each
+ *   chunk and at the end.  On return every solve's arrays hold its final
+ *   iterate (complex128 / complex64), thiim_residual(ctx[b]) reports its last
+ *   residual, iters_out[b] (optional) the iterations it ran and
+ *   residual_out[b] (optional) the residual.  Temporary device memory for the
+ *   item list and partial norms is allocated per call.
+ * Errors: THIIM_ERR_ARG (mixed precisions or devices, check_every odd or < 2),
+ * THIIM_ERR_STATE, THIIM_ERR_NOMEM, THIIM_ERR_NONFINITE, THIIM_ERR_CUDA.
+ */
+int thiim_batch_iterate(thiim_ctx *const ctx[], int nb, int max_iters, int check_every,
+                        double tol, int *iters_out, double *residual_out);
+
+/*
  * thiim_step_noalloc — one THIIM iteration that allocates no memory.
  *   For callers that cannot call cudaMalloc (code running under another
  *   framework's memory pool or allocator hooks, or with all device memory

@@ -46,6 +46,8 @@ template <typename R>
 struct Native {
     typedef typename cplx_of<R>::type Z;
     static constexpr bool pairs = false;
+    // resident 256-thread CTAs per SM asked of the register allocator
+    static constexpr int min_blocks = sizeof(R) == 8 ? 3 : 5;
     __device__ static __forceinline__ Z zero() { Z z; z.x = R(0); z.y = R(0); return z; }
     __device__ static __forceinline__ Z ld_field(const void *b, size_t i) { return ldg_as<Z>(b, i); }
     __device__ static __forceinline__ Z ld_coef(const void *b, size_t i) { return ldg_as<Z>(b, i); }
@@ -138,6 +140,7 @@ template <int IN_PAIRS, int OUT_PAIRS>
 struct PairArith {
     typedef zpair Z;
     static constexpr bool pairs = true;
+    static constexpr int min_blocks = 2;
     __device__ static __forceinline__ Z zero() { Z z; z.x.h = z.x.l = z.y.h = z.y.l = 0.f; return z; }
     __device__ static __forceinline__ Z from_f4(float4 v) { Z z; z.x.h = v.x; z.x.l = v.y; z.y.h = v.z; z.y.l = v.w; return z; }
     __device__ static __forceinline__ Z ld_field(const void *b, size_t i) {

@@ -125,9 +125,12 @@ struct SplitIO {
     }
 };
 
-template <typename A, int TX, int TY, int NT, int MINB, int MODE = SWEEP_PLAIN>
-__global__ void __launch_bounds__(NT, MINB)
-sweep_kernel(const SweepArgs a) {
+// One CTA's share of an iteration: the TX x TY column `tile` over the z
+// chunk `chunk`.  partial_out (2 doubles) receives the CTA's |dF|^2, |F|^2
+// when non-null.  Used by the per-problem kernel below and by the batched
+// persistent kernel (thiim_batch.cu).
+template <typename A, int TX, int TY, int NT, int MODE>
+__device__ __forceinline__ void sweep_tile(const SweepArgs &a, int tile, int chunk, double *partial_out) {
     typedef typename A::Z Z;
     typedef SplitIO<A, MODE> IO;
     constexpr int EW = TX + 2, EH = TY + 2;   // E^n region: -1 .. TX (x), -1 .. TY (y)
@@ -138,17 +141,16 @@ sweep_kernel(const SweepArgs a) {
 
     const int nx = a.nx, ny = a.ny, nz = a.nz;
     const bool px = a.bc & 1u, py = a.bc & 2u, pz = a.bc & 4u;
-    const int tile = blockIdx.x;
     const int i0 = (tile % a.tiles_x) * TX;
     const int j0 = (tile / a.tiles_x) * TY;
     const int nix = min(TX, nx - i0), niy = min(TY, ny - j0);
-    const int z0 = blockIdx.y * a.zchunk;
+    const int z0 = chunk * a.zchunk;
     const int z1 = min(z0 + a.zchunk, nz);
     const size_t plane = (size_t)nx * ny;
     const int ew = nix + 2, ecount = (nix + 2) * (niy + 2);
     const int hw = nix + 1, hcount = (nix + 1) * (niy + 1);
     const int tcount = nix * niy;
-    const bool want_norm = a.partials != nullptr;
+    const bool want_norm = partial_out != nullptr;
     double acc_d = 0.0, acc_x = 0.0;
 
     // Phase A: full E^n on the E region of plane k into sE[b].
@@ -280,11 +282,17 @@ sweep_kernel(const SweepArgs a) {
         if (threadIdx.x == 0) {
             double d = 0.0, x = 0.0;
             for (int i = 0; i < NT / 32; ++i) { d += red[0][i]; x += red[1][i]; }
-            const size_t cta = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
-            a.partials[2 * cta] = d;
-            a.partials[2 * cta + 1] = x;
+            partial_out[0] = d;
+            partial_out[1] = x;
         }
     }
+}
+
+template <typename A, int TX, int TY, int NT, int MINB, int MODE = SWEEP_PLAIN>
+__global__ void __launch_bounds__(NT, (MINB > 0 ? MINB : (NT == 256 ? A::min_blocks : 1)))
+sweep_kernel(const SweepArgs a) {
+    const size_t cta = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
+    sweep_tile<A, TX, TY, NT, MODE>(a, blockIdx.x, blockIdx.y, a.partials ? a.partials + 2 * cta : nullptr);
 }
 
 }  // namespace thiim

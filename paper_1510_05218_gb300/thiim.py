@@ -66,6 +66,10 @@ def load_library(build_if_missing: bool = False):
     lib.thiim_mixed_solve.argtypes = [vp, P28, P12, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                       ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
     lib.thiim_mixed_solve.restype = ctypes.c_int
+    lib.thiim_batch_iterate.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                        ctypes.c_double, ctypes.POINTER(ctypes.c_int),
+                                        ctypes.POINTER(ctypes.c_double)]
+    lib.thiim_batch_iterate.restype = ctypes.c_int
     lib.thiim_destroy.argtypes = [vp]
     lib.thiim_destroy.restype = None
     lib.thiim_strerror.argtypes = [ctypes.c_int]
@@ -169,6 +173,17 @@ def thiim_mixed_solve(ctx, coeffs64, x64, inner_iters=50, max_outer=1, tol=0.0):
         ctx, _ptrs(coeffs64, 28, "coefficient"), _ptrs(x64, 12, "field"), int(inner_iters), int(max_outer),
         float(tol), ctypes.byref(done), ctypes.byref(r)))
     return done.value, r.value
+
+
+def thiim_batch_iterate(ctxs, max_iters, check_every=50, tol=0.0):
+    """Advance several solves together; returns (iterations per solve, residual per solve)."""
+    n = len(ctxs)
+    arr = (ctypes.c_void_p * n)(*[c.value if hasattr(c, "value") else c for c in ctxs])
+    iters = (ctypes.c_int * n)()
+    res = (ctypes.c_double * n)()
+    _check("thiim_batch_iterate", load_library().thiim_batch_iterate(arr, n, int(max_iters), int(check_every),
+                                                                      float(tol), iters, res))
+    return list(iters), list(res)
 
 
 def thiim_step_noalloc(nx, ny, nz, precision, bc_flags, src, dst, coeffs, stream=None, want_residual=True):
