@@ -3,7 +3,11 @@
 Workload (default): the 512^3 textured thin-film stack in complex128 — 12
 split fields + 28 coefficient arrays, 86 GB resident in HBM — with the
 plane-wave source; one step = thiim_iterate(200) followed by thiim_residual
-(the FP64 relative update of the last iteration).  MLUP/s = cells x
+(the FP64 relative update of the last iteration).  The headline path keeps
+complex128 data and computes on FP32 pairs (GB300's FP64 rate caps the
+native FP64 sweep near 43 % of the HBM roofline); "variants" reports native
+FP64, complex64, mixed precision with FP64 defect correction and the
+32-solve batch, each measured after one warm-up.  MLUP/s = cells x
 iterations / time.  Every input array is larger than L2, so no flush is
 needed between steps.
 
@@ -33,6 +37,9 @@ DTYPE = {"c128": "f64", "pair": "f32x2", "c64": "f32"}
 PRECISION_CODE = {"c128": 0, "c64": 1, "pair": 2}
 KERNEL = {"c128": "sweep_kernel<Native<double>>", "pair": "sweep_kernel<PairArith<1,1>>",
           "c64": "sweep_kernel<Native<float>>"}
+PRECISION_NOTE = {"c128": "with native FP64 arithmetic",
+                  "pair": "with FP32-pair arithmetic (parity with the FP64 oracle <= 1e-12)",
+                  "c64": "stored as complex64 with FP32 arithmetic"}
 FLOPS_PER_LUP = 248                                  # the paper's count (Sec. III-A)
 SWEEP_SRC = os.path.join(ROOT, "paper_1510_05218_gb300", "csrc", "thiim_sweep.cuh")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "sweep_traffic.json")
@@ -185,6 +192,132 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def _clock_index(local):
+    return local if os.environ.get("CUDA_VISIBLE_DEVICES") is None else 0
+
+
+def _stack_problem(p, torch, st, precision, stream, dev):
+    """Context + device arrays of a layered stack, coefficients built on the GPU."""
+    prec = PRECISION_CODE[precision]
+    dt = torch.complex64 if prec == p.THIIM_C64 else torch.complex128
+    shape = (st.nz, st.ny, st.nx)
+    eps = torch.from_numpy(st.eps()).to(dev)
+    ctx = p.thiim_create(st.nx, st.ny, st.nz, prec, 3, stream)
+    co = [torch.empty(shape, dtype=dt, device=dev) for _ in range(28)]
+    fields = [torch.zeros(shape, dtype=dt, device=dev) for _ in range(12)]
+    with torch.cuda.stream(stream):
+        p.thiim_build_coeffs(ctx, eps, st.sigma_pml_e(), st.sigma_pml_h(), st.omega, st.tau, st.k_s, 1.0, co)
+    p.thiim_set_coeffs(ctx, co)
+    p.thiim_set_fields(ctx, fields)
+    torch.cuda.synchronize()
+    return ctx, co, fields, eps
+
+
+def _time_iterate(p, torch, ctx, stream, iters, warmup, steps):
+    """CUDA-event time of thiim_iterate(iters) + thiim_residual, per step."""
+    for _ in range(warmup):
+        p.thiim_iterate(ctx, iters)
+        p.thiim_residual(ctx)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    res = []
+    t0.record(stream)
+    for s in range(steps):
+        ev[s][0].record(stream)
+        p.thiim_iterate(ctx, iters)
+        ev[s][1].record(stream)
+        res.append(p.thiim_residual(ctx))
+    t1.record(stream)
+    torch.cuda.synchronize()
+    return t0.elapsed_time(t1), sum(a.elapsed_time(b) for a, b in ev), res
+
+
+def _variant_sweep(p, torch, st, precision, stream, dev, iters, warmup, steps, peak):
+    ctx, co, fields, eps = _stack_problem(p, torch, st, precision, stream, dev)
+    del eps
+    try:
+        ms_total, ms_iter, res = _time_iterate(p, torch, ctx, stream, iters, warmup, steps)
+    finally:
+        p.thiim_destroy(ctx)
+    cells = st.nx * st.ny * st.nz
+    launch_s = ms_iter / 1e3 / (steps * iters)
+    achieved = BYTES_PER_LUP[precision] * cells / launch_s / 1e9
+    del co, fields
+    torch.cuda.empty_cache()
+    return {"value": cells * iters * steps / (ms_total / 1e3) / 1e6, "unit": "MLUP/s", "dtype": DTYPE[precision],
+            "kernel": KERNEL[precision], "launch_ms": launch_s * 1e3, "achieved_gbs": achieved,
+            "frac_hbm": achieved / peak, "residual_last": res[-1], "steps": steps, "warmup": warmup}
+
+
+def _variant_mixed(p, torch, st, stream, dev, inner, outer, warmup):
+    """complex64 corrections with FP64 defect correction at this grid."""
+    shape = (st.nz, st.ny, st.nx)
+    eps = torch.from_numpy(st.eps()).to(dev)
+    ctx64 = p.thiim_create(st.nx, st.ny, st.nz, p.THIIM_C128, 3, stream)
+    co64 = [torch.empty(shape, dtype=torch.complex128, device=dev) for _ in range(28)]
+    with torch.cuda.stream(stream):
+        p.thiim_build_coeffs(ctx64, eps, st.sigma_pml_e(), st.sigma_pml_h(), st.omega, st.tau, st.k_s, 1.0, co64)
+    p.thiim_destroy(ctx64)
+    ctx = p.thiim_create(st.nx, st.ny, st.nz, p.THIIM_C64, 3, stream)
+    co32 = [torch.empty(shape, dtype=torch.complex64, device=dev) for _ in range(28)]
+    work = [torch.zeros(shape, dtype=torch.complex64, device=dev) for _ in range(12)]
+    x64 = [torch.zeros(shape, dtype=torch.complex128, device=dev) for _ in range(12)]
+    try:
+        with torch.cuda.stream(stream):
+            p.thiim_build_coeffs(ctx, eps, st.sigma_pml_e(), st.sigma_pml_h(), st.omega, st.tau, st.k_s, 1.0, co32)
+        del eps
+        p.thiim_set_coeffs(ctx, co32)
+        p.thiim_set_fields(ctx, work)
+        for _ in range(warmup):
+            p.thiim_mixed_solve(ctx, co64, x64, inner, 1, 0.0)
+        torch.cuda.synchronize()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        done, r = p.thiim_mixed_solve(ctx, co64, x64, inner, outer, 0.0)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        ms = t0.elapsed_time(t1)
+    finally:
+        p.thiim_destroy(ctx)
+    cells = st.nx * st.ny * st.nz
+    del co64, co32, work, x64
+    torch.cuda.empty_cache()
+    return {"value": cells * inner * done / (ms / 1e3) / 1e6, "unit": "MLUP/s", "dtype": "f32+f64",
+            "inner_iters": inner, "outer": done, "fp64_defects": done + 1, "residual_last": r,
+            "what": "MLUP/s counts the %d complex64 iterations per outer step; each outer step also runs one "
+                    "FP64 defect sweep and a fold" % inner}
+
+
+def _variant_batch(p, torch, precision, stream, dev, iters, check, warmup):
+    """The 32-solve spectrum sweep (uneven grids) in one persistent launch per iteration."""
+    from workloads import batch_configs
+    stacks = batch_configs(32, seed=1)
+    probs = [_stack_problem(p, torch, st, precision, stream, dev) for st in stacks]
+    ctxs = [pr[0] for pr in probs]
+    cells = sum(st.nx * st.ny * st.nz for st in stacks)
+    try:
+        for _ in range(warmup):
+            p.thiim_batch_iterate(ctxs, check, check, 0.0)
+        torch.cuda.synchronize()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        its, res = p.thiim_batch_iterate(ctxs, iters, check, 0.0)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        ms = t0.elapsed_time(t1)
+    finally:
+        for c in ctxs:
+            p.thiim_destroy(c)
+    del probs
+    torch.cuda.empty_cache()
+    return {"value": cells * iters / (ms / 1e3) / 1e6, "unit": "MLUP/s", "dtype": DTYPE[precision],
+            "solves": len(stacks), "cells_total": cells, "iters": iters, "check_every": check,
+            "grids": "Nx=Ny in [%d, %d], Nz in [%d, %d]" % (min(s.nx for s in stacks), max(s.nx for s in stacks),
+                                                          min(s.nz for s in stacks), max(s.nz for s in stacks)),
+            "residual_max": max(res)}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -207,20 +340,11 @@ def run_ours(args):
     cells = st.nx * st.ny * st.nz
     iters = args.iters
     stream = torch.cuda.Stream(device=dev)
+    peak, peak_kind = _peaks()
 
-    eps_host = torch.from_numpy(st.eps())
-    eps_pinned = eps_host.pin_memory()
-    del eps_host
-    eps = eps_pinned.to(dev)
-    ctx = p.thiim_create(st.nx, st.ny, st.nz, prec, 3, stream)
-    co = [torch.empty(shape, dtype=dt, device=dev) for _ in range(28)]
-    fields = [torch.zeros(shape, dtype=dt, device=dev) for _ in range(12)]
+    ctx, co, fields, eps = _stack_problem(p, torch, st, args.precision, stream, dev)
+    eps_pinned = eps.cpu().pin_memory()
     sig_e, sig_h = st.sigma_pml_e(), st.sigma_pml_h()
-    with torch.cuda.stream(stream):
-        p.thiim_build_coeffs(ctx, eps, sig_e, sig_h, st.omega, st.tau, st.k_s, 1.0, co)
-    p.thiim_set_coeffs(ctx, co)
-    p.thiim_set_fields(ctx, fields)
-    torch.cuda.synchronize()
 
     def barrier():
         if world > 1:
@@ -232,27 +356,13 @@ def run_ours(args):
         p.thiim_iterate(ctx, iters)
         p.thiim_residual(ctx)
     torch.cuda.synchronize()
-    sampler = ClockSampler(local if os.environ.get("CUDA_VISIBLE_DEVICES") is None else 0)
+    sampler = ClockSampler(_clock_index(local))
     sampler.start()
     time.sleep(0.3)
     barrier()
-    torch.cuda.synchronize()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    t_start = torch.cuda.Event(enable_timing=True)
-    t_stop = torch.cuda.Event(enable_timing=True)
-    t_start.record(stream)
-    residuals = []
-    for s in range(args.steps):
-        ev[s][0].record(stream)
-        p.thiim_iterate(ctx, iters)
-        ev[s][1].record(stream)
-        residuals.append(p.thiim_residual(ctx))
-    t_stop.record(stream)
-    torch.cuda.synchronize()
+    ms_total, ms_iter_calls, residuals = _time_iterate(p, torch, ctx, stream, iters, 0, args.steps)
     barrier()
     clocks = sampler.stop()
-    ms_total = t_start.elapsed_time(t_stop)
-    ms_iter_calls = sum(a.elapsed_time(b) for a, b in ev)
     if world > 1:
         import torch.distributed as dist
         t = torch.tensor([ms_total], device=dev, dtype=torch.float64)
@@ -264,7 +374,6 @@ def run_ours(args):
     # roofline of the dominant kernel (the fused sweep): one launch per iteration
     launch_s = ms_iter_calls / 1e3 / (args.steps * iters)
     alg_bytes = BYTES_PER_LUP[args.precision] * cells
-    peak, peak_kind = _peaks()
     achieved = alg_bytes / launch_s / 1e9
     kernel_key = KERNEL[args.precision]
     traffic = _traffic(kernel_key, cells)
@@ -308,6 +417,17 @@ def run_ours(args):
         del host_fields
 
     p.thiim_destroy(ctx)
+    del co, fields, eps
+    torch.cuda.empty_cache()
+
+    variants = {}
+    if not args.no_variants:
+        for mode in ("c128", "pair", "c64"):
+            if mode != args.precision:
+                variants[mode] = _variant_sweep(p, torch, st, mode, stream, dev, iters, 1, 1, peak)
+        variants["mixed_c64_f64_defect"] = _variant_mixed(p, torch, st, stream, dev, 50, 4, 1)
+        variants["batch32_" + args.precision] = _variant_batch(p, torch, args.precision, stream, dev, 200, 50, 1)
+
     if rank != 0:
         return
 
@@ -324,9 +444,9 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": "MLUP/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": DTYPE[args.precision], "data": "synthetic",
-        "config": {"workload": "%s: %dx%dx%d textured thin-film stack (seeded sinusoid texture), %s, "
-                               "%d THIIM iterations + FP64 residual per step" % (
-                                   args.workload, st.nx, st.ny, st.nz, args.precision, iters),
+        "config": {"workload": "%s: %dx%dx%d textured thin-film stack (seeded sinusoid texture), complex128 data "
+                               "%s, %d THIIM iterations + FP64 residual per step" % (
+                                   args.workload, st.nx, st.ny, st.nz, PRECISION_NOTE[args.precision], iters),
                    "grid": [st.nx, st.ny, st.nz], "iters_per_step": iters, "precision": args.precision,
                    "kernel": "fused out-of-place z-streaming sweep, one launch per iteration",
                    "l2": "inputs larger than L2 (no flush needed)",
@@ -341,6 +461,7 @@ def run_ours(args):
         "e2e": e2e,
         "gpu_launches": args.steps * (iters + 1),
         "cpu_baseline": cpu,
+        "variants": variants,
     }
     print(json.dumps(out), flush=True)
     if world > 1:
@@ -355,7 +476,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="stack512")
-    ap.add_argument("--precision", default="c128", choices=["c128", "pair", "c64"])
+    ap.add_argument("--precision", default="pair", choices=["c128", "pair", "c64"])
+    ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--iters", type=int, default=200)
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--e2e-warmup", type=int, default=1)
