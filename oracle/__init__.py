@@ -8,7 +8,9 @@ links or executes anything here, and nothing here imports the product.
   Listings 1-2), compiled by ``build.py`` with gcc.
 * ``coeffs.py``       the per-cell coefficient arrays t, c and the source
   arrays derived from Eqs. 3-5, in NumPy FP64.
-* ``adjoint.py``      the transposed iteration and parameter gradients.
+  ``thiim_oracle.c`` also holds the adjoint of one iteration (reverse mode)
+  with the coefficient gradients; ``coeffs.py`` the derivatives of the
+  coefficients with respect to the real permittivity.
 """
-from .thiim_oracle import iterate, rule, SPLITS, FIELD_INDEX, COEFF_NAMES  # noqa: F401
-from .coeffs import build_coeffs, incident_wave, discrete_omega  # noqa: F401
+from .thiim_oracle import iterate, adjoint_step, rule, SPLITS, FIELD_INDEX, COEFF_NAMES  # noqa: F401
+from .coeffs import build_coeffs, coeff_eps_derivatives, incident_wave, discrete_omega  # noqa: F401

@@ -131,3 +131,40 @@ def stack_coeffs(stack):
     """Coefficients of a workloads.LayeredStack with its plane-wave source."""
     return build_coeffs(stack.eps(), stack.sigma_pml_e(), stack.sigma_pml_h(),
                         stack.omega, stack.tau, tfsf=(stack.k_s, 1.0))
+
+
+def coeff_eps_derivatives(eps_r, sigma_pml_e, omega, tau, tfsf=None):
+    """d(coefficient)/d(Re eps) for the arrays that depend on the permittivity.
+
+    Returns {array index: derivative array} for t and c of the six E splits
+    and, with a plane-wave source, SrcExy (proportional to c_Exy at k_s).
+    Differentiating the E coefficients of Eqs. 3 and 5 with sigma held fixed:
+      eps > 0:  dt/deps = e(-w tau) (tau sig / eps^2) / (1 + tau sig/eps)^2
+                dc/deps = -tau e(-w tau/2) / (eps + tau sig)^2
+      eps < 0:  dt/deps = -e(+w tau) (tau sig / eps^2) / (1 - tau sig/eps)^2
+                dc/deps = tau e(+w tau/2) / (eps - tau sig)^2
+    """
+    eps_r = np.asarray(eps_r, np.complex128)
+    eps = eps_r.real
+    sig_mat = omega * eps_r.imag
+    sz_e = np.asarray(sigma_pml_e, np.float64)[:, None, None]
+    ph = lambda a: np.exp(1j * a)  # noqa: E731
+    out = {}
+    for s in range(6, 12):
+        d = rule(s)[0]
+        sig = sig_mat + (sz_e if d == 2 else 0.0)
+        fwd = eps > 0
+        dt_f = ph(-omega * tau) * (tau * sig / eps ** 2) / (1.0 + tau * sig / eps) ** 2
+        dc_f = -tau * ph(-omega * tau / 2.0) / (eps + tau * sig) ** 2
+        dt_b = -ph(omega * tau) * (tau * sig / eps ** 2) / (1.0 - tau * sig / eps) ** 2
+        dc_b = tau * ph(omega * tau / 2.0) / (eps - tau * sig) ** 2
+        out[s] = np.where(fwd, dt_f, dt_b)
+        out[12 + s] = np.where(fwd, dc_f, dc_b)
+    if tfsf is not None:
+        k_s, amp = tfsf
+        _, h_inc = incident_wave(omega, tau, k_s, amp)
+        s_e = SPLITS.index("Exy")
+        dsrc = np.zeros(eps.shape, np.complex128)
+        dsrc[k_s] = -rule(s_e)[3] * out[12 + s_e][k_s] * h_inc(k_s)
+        out[26] = dsrc
+    return out

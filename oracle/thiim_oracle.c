@@ -144,3 +144,123 @@ int oracle_rule(int s, int *d, int *src_a, int *src_b, int *sign, int *src_arr)
     *sign = RULES[s].sign; *src_arr = RULES[s].src_arr;
     return 0;
 }
+
+/* ------------------------------------------------------------------------
+ * Adjoint of one iteration (reverse-mode derivative of x^{n+1} = F(x^n)).
+ *
+ * With H' = T_H H + C_H D^- E + b_H and E' = T_E E + C_E D^+ H' + b_E (each
+ * split s: x_s' = t_s x_s + Src_s + sign_s c_s D(F)), and adjoints mu of x^{n+1}
+ * (mu = dJ/d conj(x), any fixed real multiple), the reverse iteration is
+ *   lh_s  = mu_Hs + sum over E splits e reading H component a(s):
+ *              sign_e (D^+_{d(e)})^T (conj(c_e) mu_e)
+ *   lam_Hs = conj(t_s) lh_s                                   (H, iterate n)
+ *   lam_Es = conj(t_s) mu_Es + sum over H splits h reading E component a(s):
+ *              sign_h (D^-_{d(h)})^T (conj(c_h) lh_h)         (E, iterate n)
+ * with (D^+)^T g = -D^- g and (D^-)^T g = -D^+ g (zero or periodic edges as in
+ * the forward).  The coefficient gradients, accumulated with +=, are
+ *   H split h:  g_t += lh_h conj(H_h^n),  g_c += lh_h conj(sign_h D^-_{d(h)} E^n),
+ *               g_Src += lh_h (Hxy, Hyx)
+ *   E split e:  g_t += mu_e conj(E_e^n),  g_c += mu_e conj(sign_e D^+_{d(e)} H^{n+1/2}),
+ *               g_Src += mu_e (Exy, Eyx)
+ * where H^{n+1/2} is the H part of x^{n+1}.
+ * ------------------------------------------------------------------------ */
+
+/* value of array a at (i, j, k) with the boundary rule; zero outside */
+static cplx at(const cplx *a, long i, long j, long k, int nx, int ny, int nz, unsigned bc)
+{
+    if (i < 0 || i >= nx) { if (!(bc & 1u)) return 0; i = (i + nx) % nx; }
+    if (j < 0 || j >= ny) { if (!(bc & 2u)) return 0; j = (j + ny) % ny; }
+    if (k < 0 || k >= nz) { if (!(bc & 4u)) return 0; k = (k + nz) % nz; }
+    return a[((size_t)k * ny + j) * nx + i];
+}
+
+int oracle_adjoint_step(int nx, int ny, int nz, unsigned bc, cplx *const *lam, cplx *const *grad,
+                        cplx *const *x_n, cplx *const *x_np1, cplx *const *co)
+{
+    if (nx <= 0 || ny <= 0 || nz <= 0) return -1;
+    const size_t n = (size_t)nx * ny * nz;
+    cplx *w[12], *lh[6];
+    for (int s = 0; s < 12; s++) w[s] = NULL;
+    for (int s = 0; s < 6; s++) lh[s] = NULL;
+    int ok = 1;
+    for (int s = 6; s < 12; s++) ok &= (w[s] = (cplx *)calloc(n, sizeof(cplx))) != NULL;
+    for (int s = 0; s < 6; s++) ok &= (lh[s] = (cplx *)calloc(n, sizeof(cplx))) != NULL;
+    if (!ok) goto fail;
+
+    /* w_e = conj(c_e) mu_e for the six E splits */
+    for (int e = 6; e < 12; e++)
+        for (size_t p = 0; p < n; p++) w[e][p] = conj(co[12 + e][p]) * lam[e][p];
+
+    /* lh_h = mu_h + sum_e sign_e (-(D^-_{d(e)} w_e)), over E splits e whose source
+     * component contains h */
+    for (int h = 0; h < 6; h++) {
+        for (int k = 0; k < nz; k++)
+            for (int j = 0; j < ny; j++)
+                for (int i = 0; i < nx; i++) {
+                    size_t p = ((size_t)k * ny + j) * nx + i;
+                    cplx acc = lam[h][p];
+                    for (int e = 6; e < 12; e++) {
+                        const split_rule r = RULES[e];
+                        if (r.src_a != h && r.src_b != h) continue;
+                        const int ox = r.d == DX, oy = r.d == DY, oz = r.d == DZ;
+                        cplx dm = at(w[e], i, j, k, nx, ny, nz, bc) - at(w[e], i - ox, j - oy, k - oz, nx, ny, nz, bc);
+                        acc += (double)r.sign * (-dm);
+                    }
+                    lh[h][p] = acc;
+                }
+    }
+    /* H gradients (need E^n differences) and lambda_H */
+    for (int h = 0; h < 6; h++) {
+        const split_rule r = RULES[h];
+        const int ox = r.d == DX, oy = r.d == DY, oz = r.d == DZ;
+        for (int k = 0; k < nz; k++)
+            for (int j = 0; j < ny; j++)
+                for (int i = 0; i < nx; i++) {
+                    size_t p = ((size_t)k * ny + j) * nx + i;
+                    cplx D = full_at(x_n, r.src_a, r.src_b, i, j, k, nx, ny, nz, bc) -
+                             full_at(x_n, r.src_a, r.src_b, i - ox, j - oy, k - oz, nx, ny, nz, bc);
+                    grad[h][p] += lh[h][p] * conj(x_n[h][p]);
+                    grad[12 + h][p] += lh[h][p] * conj((double)r.sign * D);
+                    if (r.src_arr >= 0) grad[r.src_arr][p] += lh[h][p];
+                }
+    }
+    /* lambda_E = conj(t_e) mu_e + sum_h sign_h (-(D^+_{d(h)} v_h)), v_h = conj(c_h) lh_h,
+     * over H splits h whose source component contains e; E gradients */
+    for (int e = 6; e < 12; e++) {
+        const split_rule r = RULES[e];
+        const int ox = r.d == DX, oy = r.d == DY, oz = r.d == DZ;
+        for (int k = 0; k < nz; k++)
+            for (int j = 0; j < ny; j++)
+                for (int i = 0; i < nx; i++) {
+                    size_t p = ((size_t)k * ny + j) * nx + i;
+                    cplx mu = lam[e][p];
+                    cplx D = full_at(x_np1, r.src_a, r.src_b, i + ox, j + oy, k + oz, nx, ny, nz, bc) -
+                             full_at(x_np1, r.src_a, r.src_b, i, j, k, nx, ny, nz, bc);
+                    grad[e][p] += mu * conj(x_n[e][p]);
+                    grad[12 + e][p] += mu * conj((double)r.sign * D);
+                    if (r.src_arr >= 0) grad[r.src_arr][p] += mu;
+                    cplx acc = conj(co[e][p]) * mu;
+                    for (int h = 0; h < 6; h++) {
+                        const split_rule q = RULES[h];
+                        if (q.src_a != e && q.src_b != e) continue;
+                        const int qx = q.d == DX, qy = q.d == DY, qz = q.d == DZ;
+                        /* v_h at (p + e_d) and p */
+                        cplx v1 = conj(at(co[12 + h], i + qx, j + qy, k + qz, nx, ny, nz, bc)) *
+                                  at(lh[h], i + qx, j + qy, k + qz, nx, ny, nz, bc);
+                        cplx v0 = conj(co[12 + h][p]) * lh[h][p];
+                        acc += (double)q.sign * (-(v1 - v0));
+                    }
+                    w[e][p] = acc;          /* new lambda_E, stored after the loop */
+                }
+    }
+    for (int e = 6; e < 12; e++) memcpy(lam[e], w[e], n * sizeof(cplx));
+    for (int h = 0; h < 6; h++)
+        for (size_t p = 0; p < n; p++) lam[h][p] = conj(co[h][p]) * lh[h][p];
+    for (int s = 6; s < 12; s++) free(w[s]);
+    for (int s = 0; s < 6; s++) free(lh[s]);
+    return 0;
+fail:
+    for (int s = 6; s < 12; s++) free(w[s]);
+    for (int s = 0; s < 6; s++) free(lh[s]);
+    return -2;
+}

@@ -31,6 +31,8 @@ def _load():
         ip = ctypes.POINTER(ctypes.c_int)
         lib.oracle_rule.argtypes = [ctypes.c_int, ip, ip, ip, ip, ip]
         lib.oracle_rule.restype = ctypes.c_int
+        lib.oracle_adjoint_step.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_uint, pp, pp, pp, pp, pp]
+        lib.oracle_adjoint_step.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -70,3 +72,16 @@ def rule(s: int):
     if lib.oracle_rule(s, *[ctypes.byref(x) for x in v]) != 0:
         raise ValueError(s)
     return tuple(x.value for x in v)
+
+
+def adjoint_step(lam, grad, x_n, x_np1, coeffs, bc: int = 3) -> None:
+    """Reverse one iteration in place: lam (12 arrays) goes from the adjoint of
+    x^{n+1} to that of x^n; grad (28 arrays) accumulates the coefficient
+    gradients.  x_n, x_np1: the forward iterates n and n+1."""
+    lib = _load()
+    shape = lam[0].shape
+    nz, ny, nx = shape
+    rc = lib.oracle_adjoint_step(nx, ny, nz, bc, _ptrs(lam, shape), _ptrs(grad, shape), _ptrs(x_n, shape),
+                                 _ptrs(x_np1, shape), _ptrs(coeffs, shape))
+    if rc != 0:
+        raise ValueError("oracle_adjoint_step failed (%d)" % rc)
