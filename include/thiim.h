@@ -83,6 +83,8 @@ enum thiim_status {
 /* Number of field / coefficient arrays (Sec. III). */
 #define THIIM_N_FIELDS 12
 #define THIIM_N_COEFFS 28
+/* Longest segment thiim_adjoint_iterate recomputes from one checkpoint. */
+#define THIIM_MAX_ADJOINT_SEGMENT 64
 
 /*
  * thiim_create — make a context for an nx * ny * nz grid.
@@ -196,6 +198,49 @@ int thiim_build_coeffs(thiim_ctx *ctx, const void *eps_r,
 int thiim_mixed_solve(thiim_ctx *ctx, void *const coeff64[THIIM_N_COEFFS],
                       void *const x64[THIIM_N_FIELDS], int inner_iters, int max_outer,
                       double tol, int *outer_done, double *rel_residual);
+
+/*
+ * thiim_adjoint_iterate — reverse n_back iterations (adjoint / reverse-mode
+ * derivative of x^{n} = F^{n_back}(x^{n0}), n = n0 + n_back).  Not in the
+ * paper; it turns the sweep into a differentiable solver.
+ *   ctx:            THIIM_C128 context with coefficients set.
+ *   lambda:         12 complex128 arrays: on entry the adjoint of x^{n}
+ *                   (the gradient of a real objective J with respect to
+ *                   conj(x), times any fixed real factor — e.g. torch's
+ *                   complex gradient, which is 2 dJ/dconj(x)); on return the
+ *                   adjoint of x^{n0}, in place.
+ *   grad_coeff:     28 complex128 arrays; the same-convention gradients of J
+ *                   with respect to each coefficient array are ADDED to them.
+ *   fwd_checkpoint: the forward iterate x^{n0} (12 complex128 arrays, read
+ *                   only).  The library recomputes x^{n0+1} .. x^{n} from it
+ *                   with the FP64 sweep into its own scratch (n_back field
+ *                   sets, kept for later calls), then runs the n_back reverse
+ *                   steps: per step one kernel for the H part and one for the
+ *                   E part (see csrc/thiim_adjoint.cu for the formulas).
+ *   n_back:         1 .. THIIM_MAX_ADJOINT_SEGMENT.
+ * Enqueued on the context's stream.  Errors: THIIM_ERR_ARG (not a
+ * THIIM_C128 context, bad n_back, NULL), THIIM_ERR_ALIGN, THIIM_ERR_STATE,
+ * THIIM_ERR_NOMEM, THIIM_ERR_CUDA.
+ */
+int thiim_adjoint_iterate(thiim_ctx *ctx, void *const lambda[THIIM_N_FIELDS],
+                          void *const grad_coeff[THIIM_N_COEFFS],
+                          const void *const fwd_checkpoint[THIIM_N_FIELDS], int n_back);
+
+/*
+ * thiim_build_coeffs_grad — chain rule through thiim_build_coeffs: given the
+ * gradients G_a of a real objective with respect to the 28 complex128
+ * coefficient arrays (torch's complex convention, 2 dJ/dconj(a)), write
+ *   grad_eps_re[p] = dJ / d Re(eps_r[p]) = Re sum_a conj(G_a[p]) d a[p] / d Re(eps_r[p])
+ * for every cell (device array of nx*ny*nz doubles), holding Im(eps_r) and
+ * hence the material conductivity fixed.  Only the six E splits' t and c (and
+ * SrcExy at the source plane) depend on the permittivity (Eqs. 3 and 5).
+ * The other arguments are those given to thiim_build_coeffs (sigma_pml_h is
+ * not needed).  Enqueued on the context's stream.
+ * Errors: THIIM_ERR_ARG, THIIM_ERR_ALIGN, THIIM_ERR_NOMEM, THIIM_ERR_CUDA.
+ */
+int thiim_build_coeffs_grad(thiim_ctx *ctx, const void *eps_r, const double *sigma_pml_e,
+                            double omega, double tau, int k_s, double amp_re, double amp_im,
+                            const void *const grad_coeff[THIIM_N_COEFFS], double *grad_eps_re);
 
 /*
  * thiim_batch_iterate — advance nb independent solves together.

@@ -397,6 +397,11 @@ void thiim_destroy(thiim_ctx *c) {
         if (c->pair_co[i]) cudaFree(c->pair_co[i]);
     for (int i = 0; i < THIIM_N_FIELDS; ++i)
         if (c->mix_r[i]) cudaFree(c->mix_r[i]);
+    for (int i = 0; i < 6; ++i)
+        if (c->adj_lh[i]) cudaFree(c->adj_lh[i]);
+    for (int m = 0; m < THIIM_MAX_ADJOINT_SEGMENT; ++m)
+        for (int i = 0; i < THIIM_N_FIELDS; ++i)
+            if (c->adj_states[m][i]) cudaFree(c->adj_states[m][i]);
     if (c->partials) cudaFree(c->partials);
     if (c->norms) cudaFree(c->norms);
     if (c->pml) cudaFree(c->pml);

@@ -31,6 +31,10 @@ struct thiim_ctx {
     int *flag;                   // device: error flag of the coefficient builder
     // defect-correction state (thiim_mixed_solve)
     void *mix_r[THIIM_N_FIELDS]; // complex64 defect r = F64(x) - x
+    // adjoint state (thiim_adjoint_iterate)
+    void *adj_lh[6];             // adjoint of H^{n+1/2}
+    void *adj_states[THIIM_MAX_ADJOINT_SEGMENT][THIIM_N_FIELDS];  // recomputed iterates
+    int adj_cap;                 // complete recomputed-iterate sets allocated
 };
 
 

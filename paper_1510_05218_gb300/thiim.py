@@ -70,6 +70,11 @@ def load_library(build_if_missing: bool = False):
                                         ctypes.c_double, ctypes.POINTER(ctypes.c_int),
                                         ctypes.POINTER(ctypes.c_double)]
     lib.thiim_batch_iterate.restype = ctypes.c_int
+    lib.thiim_adjoint_iterate.argtypes = [vp, P12, P28, P12, ctypes.c_int]
+    lib.thiim_adjoint_iterate.restype = ctypes.c_int
+    lib.thiim_build_coeffs_grad.argtypes = [vp, vp, vp, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                            ctypes.c_double, ctypes.c_double, P28, vp]
+    lib.thiim_build_coeffs_grad.restype = ctypes.c_int
     lib.thiim_destroy.argtypes = [vp]
     lib.thiim_destroy.restype = None
     lib.thiim_strerror.argtypes = [ctypes.c_int]
@@ -173,6 +178,24 @@ def thiim_mixed_solve(ctx, coeffs64, x64, inner_iters=50, max_outer=1, tol=0.0):
         ctx, _ptrs(coeffs64, 28, "coefficient"), _ptrs(x64, 12, "field"), int(inner_iters), int(max_outer),
         float(tol), ctypes.byref(done), ctypes.byref(r)))
     return done.value, r.value
+
+
+def thiim_adjoint_iterate(ctx, lam, grad_coeffs, checkpoint, n_back):
+    """Reverse n_back iterations in place on `lam`, accumulating into `grad_coeffs`."""
+    _check("thiim_adjoint_iterate", load_library().thiim_adjoint_iterate(
+        ctx, _ptrs(lam, 12, "lambda"), _ptrs(grad_coeffs, 28, "gradient"), _ptrs(checkpoint, 12, "field"),
+        int(n_back)))
+
+
+def thiim_build_coeffs_grad(ctx, eps_r, sigma_pml_e, omega, tau, k_s, amp, grad_coeffs, grad_eps_re):
+    """dJ/dRe(eps) per cell into the float64 CUDA tensor grad_eps_re."""
+    import numpy as np
+    se = None if sigma_pml_e is None else np.ascontiguousarray(sigma_pml_e, dtype=np.float64)
+    amp = complex(amp)
+    _check("thiim_build_coeffs_grad", load_library().thiim_build_coeffs_grad(
+        ctx, ctypes.c_void_p(eps_r.data_ptr()), None if se is None else se.ctypes.data_as(ctypes.c_void_p),
+        float(omega), float(tau), int(k_s), amp.real, amp.imag, _ptrs(grad_coeffs, 28, "gradient"),
+        ctypes.c_void_p(grad_eps_re.data_ptr())))
 
 
 def thiim_batch_iterate(ctxs, max_iters, check_every=50, tol=0.0):
