@@ -103,6 +103,20 @@ int thiim_create(thiim_ctx **out, int nx, int ny, int nz, int precision,
 int thiim_set_stream(thiim_ctx *ctx, void *cuda_stream);
 
 /*
+ * thiim_set_tuning — execution parameters of thiim_iterate (results do not
+ * depend on them; the autotuner in paper_1510_05218_gb300/tuning.py picks
+ * them by timing candidates that a footprint model admits).
+ *   temporal_block: iterations fused per pass over HBM: 1, or 2 for a
+ *                   THIIM_C64 context (temporal blocking: each CTA runs two
+ *                   staged iterations with a one-plane lag, keeping the
+ *                   intermediate iterate in shared memory; bit-identical to
+ *                   two single iterations).
+ *   zchunk:         z planes per CTA (0 = the library's default).
+ * Errors: THIIM_ERR_ARG.
+ */
+int thiim_set_tuning(thiim_ctx *ctx, int temporal_block, int zchunk);
+
+/*
  * thiim_set_coeffs — borrow the 28 coefficient arrays (device pointers, in the
  * context's precision, layout above).  Errors: THIIM_ERR_ARG on NULL,
  * THIIM_ERR_ALIGN on misalignment.

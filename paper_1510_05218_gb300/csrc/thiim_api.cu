@@ -198,7 +198,17 @@ int thiim_create(thiim_ctx **out, int nx, int ny, int nz, int precision, unsigne
         return THIIM_ERR_CUDA;
     }
     c->zchunk = default_zchunk(c);
+    c->temporal = 1;
     *out = c;
+    return THIIM_OK;
+}
+
+int thiim_set_tuning(thiim_ctx *c, int temporal_block, int zchunk) {
+    if (!c || zchunk < 0 || zchunk > c->nz) return THIIM_ERR_ARG;
+    if (temporal_block != 1 && temporal_block != 2) return THIIM_ERR_ARG;
+    if (temporal_block == 2 && c->precision != THIIM_C64) return THIIM_ERR_ARG;
+    c->temporal = temporal_block;
+    c->zchunk = zchunk ? zchunk : default_zchunk(c);
     return THIIM_OK;
 }
 
@@ -282,19 +292,24 @@ int thiim_iterate(thiim_ctx *c, int n_iters) {
     a.zchunk = c->zchunk;
     a.tiles_x = tx;
     void **from = c->user, **to = c->alt;
-    for (int it = 0; it < n_iters; ++it) {
+    for (int it = 0; it < n_iters;) {
+        // temporal blocking: two iterations per launch while two remain
+        const int step = (c->temporal == 2 && n_iters - it >= 2) ? 2 : 1;
         memcpy(a.src, from, sizeof(a.src));
         memcpy(a.dst, to, sizeof(a.dst));
-        a.partials = (it == n_iters - 1) ? c->partials : nullptr;
+        a.partials = (it + step == n_iters) ? c->partials : nullptr;
         cudaError_t e;
         if (pair)   // intermediate iterates stay as float4 pairs; first reads and last writes complex128
             e = launch_sweep_pair(a, grid, c->stream, it > 0, it < n_iters - 1);
         else if (c->precision == THIIM_C128)
             e = launch_sweep_f64(a, grid, c->stream);
+        else if (step == 2)
+            e = launch_sweep2_f32(a, grid, c->stream);
         else
             e = launch_sweep_f32(a, grid, c->stream);
         if (e != cudaSuccess) return THIIM_ERR_CUDA;
         void **tmp = from; from = to; to = tmp;
+        it += step;
     }
     if (from != c->user) {       // odd count: the newest iterate sits in the library's set
         for (int i = 0; i < THIIM_N_FIELDS; ++i) {

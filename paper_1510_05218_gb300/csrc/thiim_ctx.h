@@ -24,6 +24,7 @@ struct thiim_ctx {
     bool pair_dirty;             // coefficients changed since they were last split
     bool have_coeffs, have_fields, have_norm;
     int zchunk;                  // planes per CTA of the sweep
+    int temporal;                // iterations per launch: 1, or 2 (temporal blocking, THIIM_C64)
     double *partials;            // 2 doubles per sweep CTA
     size_t partials_cap;         // in CTAs
     double *norms;               // device: |dF|^2, |F|^2 of the last iteration

@@ -37,6 +37,10 @@ cudaError_t launch_sweep_pair(const SweepArgs &a, dim3 grid, cudaStream_t s, boo
 cudaError_t launch_defect_f64(const SweepArgs &a, dim3 grid, cudaStream_t s);
 cudaError_t launch_correct_f32(const SweepArgs &a, dim3 grid, cudaStream_t s);
 
+// Two iterations per launch (temporal blocking), complex64 only; same grid
+// and partials layout as the single-iteration sweep.
+cudaError_t launch_sweep2_f32(const SweepArgs &a, dim3 grid, cudaStream_t s);
+
 // Split n complex128 values of each of `count` arrays into float4 pairs.
 cudaError_t split_coeffs(const void *const *src, void *const *dst, int count, size_t n, cudaStream_t s);
 

@@ -54,6 +54,7 @@ def load_library(build_if_missing: bool = False):
     lib.thiim_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                  ctypes.c_uint, vp]
     lib.thiim_set_stream.argtypes = [vp, vp]
+    lib.thiim_set_tuning.argtypes = [vp, ctypes.c_int, ctypes.c_int]
     lib.thiim_set_coeffs.argtypes = [vp, P28]
     lib.thiim_set_fields.argtypes = [vp, P12]
     lib.thiim_iterate.argtypes = [vp, ctypes.c_int]
@@ -80,7 +81,7 @@ def load_library(build_if_missing: bool = False):
     lib.thiim_strerror.argtypes = [ctypes.c_int]
     lib.thiim_strerror.restype = ctypes.c_char_p
     lib.thiim_version.argtypes = []
-    for name in ("thiim_create", "thiim_set_stream", "thiim_set_coeffs", "thiim_set_fields", "thiim_iterate",
+    for name in ("thiim_create", "thiim_set_stream", "thiim_set_tuning", "thiim_set_coeffs", "thiim_set_fields", "thiim_iterate",
                  "thiim_residual", "thiim_build_coeffs", "thiim_version"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
@@ -135,6 +136,10 @@ def thiim_create(nx, ny, nz, precision=THIIM_C128, bc_flags=THIIM_PERIODIC_X | T
 
 def thiim_set_stream(ctx, stream=None):
     _check("thiim_set_stream", load_library().thiim_set_stream(ctx, _stream_ptr(stream)))
+
+
+def thiim_set_tuning(ctx, temporal_block=1, zchunk=0):
+    _check("thiim_set_tuning", load_library().thiim_set_tuning(ctx, int(temporal_block), int(zchunk)))
 
 
 def thiim_set_coeffs(ctx, coeffs):

@@ -1,0 +1,57 @@
+"""The paper's traffic and cache models (Sec. III) and their GPU counterparts.
+
+Golden values: tests/golden/paper_numbers.json (printed in the paper).
+"""
+import json
+import os
+
+import pytest
+
+from paper_1510_05218_gb300 import tuning
+
+GOLDEN = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_numbers.json")))
+
+
+def test_code_balance_models_match_the_paper():
+    assert tuning.code_balance_naive() == GOLDEN["code_balance_naive"]
+    assert tuning.code_balance_spatial() == GOLDEN["code_balance_spatial"]
+    assert round(GOLDEN["flops_per_lup"] / tuning.code_balance_naive(), 2) == GOLDEN["intensity_naive"]
+    assert round(GOLDEN["flops_per_lup"] / tuning.code_balance_spatial(), 2) == GOLDEN["intensity_spatial"]
+    assert round(tuning.bottleneck_mlups(GOLDEN["bottleneck_bandwidth_gbs"], tuning.code_balance_spatial())) \
+        == GOLDEN["bottleneck_mlups"]
+
+
+def test_cache_block_model_worked_example_and_haswell_cases():
+    ex = GOLDEN["cache_block_example"]
+    assert tuning.cache_block_bytes(1, ex["D_w"], ex["B_Z"]) == ex["bytes_per_nx"]
+    assert ex["D_w"] + ex["B_Z"] - 1 == ex["W_w"]
+    # B_Z = 6, D_w = 4 with three thread groups (three tiles): "30 MiB";
+    # B_Z = 1, D_w = 8 with two thread groups of nine threads: "20 MiB" (both approximate)
+    c1 = 3 * tuning.cache_block_bytes(480, 4, 6) / 2 ** 20
+    c2 = 2 * tuning.cache_block_bytes(480, 8, 1) / 2 ** 20
+    assert abs(c1 - 30) <= 0.1 * 30 and abs(c2 - 20) <= 0.1 * 20
+    assert c2 > GOLDEN["usable_l3_mib"] * 0.9 and c1 > GOLDEN["usable_l3_mib"]
+
+
+def test_diamond_code_balance_decreases_with_width():
+    vals = [tuning.code_balance_diamond(d) for d in (4, 8, 12, 16)]
+    assert [round(v) for v in vals] == [428, 211, 140, 105]
+    assert vals[1] < tuning.code_balance_spatial() / 5      # "6x lower code balance" regime
+
+
+@pytest.mark.parametrize("precision,temporal", [(0, 1), (1, 1), (2, 1), (1, 2)])
+def test_gpu_footprint_and_balance(precision, temporal):
+    fp = tuning.gpu_footprint(precision, temporal, 64, 8192, 152, 129 * 2 ** 20)
+    assert fp["smem_per_cta"] <= tuning.SMEM_PER_CTA and fp["fits"]
+    b = tuning.gpu_code_balance(precision, temporal, 64)
+    alg = 52 * tuning.elem_bytes(precision)
+    if temporal == 1:
+        assert alg < b < 1.3 * alg            # the halo re-read of 32x8 tiles: +10..30 %
+    else:
+        assert b < 0.75 * alg                 # two iterations per pass: fewer bytes per iteration
+
+
+def test_candidates_respect_the_model():
+    c = tuning.candidates(1, 512, 1024, 152, 129 * 2 ** 20)
+    assert (1, 64) in c and any(t == 2 for t, _ in c)
+    assert all(t == 1 for t, _ in tuning.candidates(0, 512, 1024, 152, 129 * 2 ** 20))
