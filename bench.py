@@ -233,11 +233,19 @@ def _time_iterate(p, torch, ctx, stream, iters, warmup, steps):
     return t0.elapsed_time(t1), sum(a.elapsed_time(b) for a, b in ev), res
 
 
-def _variant_sweep(p, torch, st, precision, stream, dev, iters, warmup, steps, peak, temporal=1):
+def _variant_sweep(p, torch, st, precision, stream, dev, iters, warmup, steps, peak, temporal=1, autotune=True):
     ctx, co, fields, eps = _stack_problem(p, torch, st, precision, stream, dev)
     del eps
+    choice = None
     if temporal != 1:
         p.thiim_set_tuning(ctx, temporal, 0)
+        choice = (temporal, 0)
+    elif autotune:
+        from paper_1510_05218_gb300 import tuning
+        choice, _ = tuning.autotune(ctx, fields, st.nx, st.ny, st.nz, PRECISION_CODE[precision], iters=20,
+                                    repeats=1, stream=stream)
+        if choice[0] != 1:          # keep this variant single-iteration; temporal blocking is its own line
+            p.thiim_set_tuning(ctx, 1, choice[1])
     try:
         ms_total, ms_iter, res = _time_iterate(p, torch, ctx, stream, iters, warmup, steps)
     finally:
@@ -251,7 +259,7 @@ def _variant_sweep(p, torch, st, precision, stream, dev, iters, warmup, steps, p
             "kernel": KERNEL[precision] if temporal == 1 else "sweep2_kernel<Native<float>> (2 iterations/launch)",
             "launch_ms": launch_s * 1e3 * temporal, "achieved_gbs": achieved,
             "frac_hbm": achieved / peak, "residual_last": res[-1], "steps": steps, "warmup": warmup,
-            "iterations_per_launch": temporal,
+            "iterations_per_launch": temporal, "tuning": list(choice) if choice else None,
             "note": "achieved_gbs counts the single-iteration algorithmic bytes per LUP (an effective rate "
                     "for temporal blocking, which moves fewer DRAM bytes)" if temporal != 1 else ""}
 
