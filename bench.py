@@ -192,6 +192,22 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def _max_over_ranks(value, dev):
+    """Max of a float over all ranks (NCCL on the GPU, or gloo on the CPU); the value itself at N = 1."""
+    import torch
+    import torch.distributed as dist
+    if not dist.is_available() or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], device=dev, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _job_mlups(world, cells, iters, steps, ms_total):
+    """Whole-job throughput: every rank runs its own replica of the workload."""
+    return world * cells * iters * steps / (ms_total / 1e3) / 1e6
+
+
 def _clock_index(local):
     return local if os.environ.get("CUDA_VISIBLE_DEVICES") is None else 0
 
@@ -387,13 +403,9 @@ def run_ours(args):
     ms_total, ms_iter_calls, residuals = _time_iterate(p, torch, ctx, stream, iters, 0, args.steps)
     barrier()
     clocks = sampler.stop()
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms_total], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = _max_over_ranks(ms_total, dev)
     ms_step = ms_total / args.steps
-    value = world * cells * iters * args.steps / (ms_total / 1e3) / 1e6
+    value = _job_mlups(world, cells, iters, args.steps, ms_total)
 
     # roofline of the dominant kernel (the fused sweep): one launch per iteration
     launch_s = ms_iter_calls / 1e3 / (args.steps * iters)
@@ -425,12 +437,7 @@ def run_ours(args):
                 for hf, f in zip(host_fields, fields):
                     hf.copy_(f, non_blocking=True)
             stream.synchronize()
-            el = time.perf_counter() - t0
-            if world > 1:
-                import torch.distributed as dist
-                t = torch.tensor([el], device=dev, dtype=torch.float64)
-                dist.all_reduce(t, op=dist.ReduceOp.MAX)
-                el = float(t.item())
+            el = _max_over_ranks(time.perf_counter() - t0, dev)
             if s >= args.e2e_warmup:
                 e2e_times.append(el)
         e2e = {"value": world * cells * iters / statistics.median(e2e_times) / 1e6, "unit": "MLUP/s",

@@ -118,3 +118,34 @@ def test_batch_rejects_mixed_precisions_and_odd_chunks():
     finally:
         p.thiim_destroy(a[0])
         p.thiim_destroy(b[0])
+
+
+def test_poisoned_solve_fails_alone():
+    """A solve with a NaN coefficient is retired at its first check and the call
+    reports THIIM_ERR_NONFINITE; the other solves still run to max_iters and
+    match their single runs."""
+    p = _lib()
+    made = [_make(p, sh, bc, 95 + i, 0) for i, (sh, bc) in enumerate(zip(SHAPES[:3], BCS[:3]))]
+    made[1][4][0][1, 2, 3] = float("nan")
+    start = [[t.clone() for t in m[3]] for m in made]
+    try:
+        with pytest.raises(p.ThiimError) as e:
+            p.thiim_batch_iterate([m[0] for m in made], 8, 4, 0.0)
+        assert e.value.code == -6
+        got = [to_host(m[3]) for m in made]
+    finally:
+        for m in made:
+            p.thiim_destroy(m[0])
+    for i in (0, 2):
+        nz, ny, nx = SHAPES[i]
+        ctx = p.thiim_create(nx, ny, nz, 0, BCS[i])
+        try:
+            fd = [t.clone() for t in start[i]]
+            p.thiim_set_coeffs(ctx, made[i][4])
+            p.thiim_set_fields(ctx, fd)
+            p.thiim_iterate(ctx, 8)
+            want = to_host(fd)
+        finally:
+            p.thiim_destroy(ctx)
+        for s in range(12):
+            assert np.array_equal(got[i][s], want[s])
