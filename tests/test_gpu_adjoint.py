@@ -2,7 +2,7 @@
 
 * The GPU reverse iteration with recomputation from a checkpoint matches the
   oracle's adjoint (lambda and all 28 coefficient gradients) at 1e-10 per
-  array (spec bound for GPU vs CPU adjoint).
+  array (the required bound for GPU vs CPU adjoint).
 * The permittivity chain rule matches the oracle's analytic coefficient
   derivatives at 1e-12.
 * End to end on the 128^3 adjoint workload (texture confined to a 32x32 box,

@@ -8,7 +8,7 @@
   (u = 2^-24, see test_gpu_sweep), so the error relative to the change
   ||x_K - x_0|| is below K * 16 u; K = 3 gives 2.9e-6, taken as 5e-6.
 * At convergence the mixed solution's full field components match the
-  oracle's converged FP64 solution to 1e-6 (the benchmark spec's bound for
+  oracle's converged FP64 solution to 1e-6 (the required bound for
   complex64 vs FP64).  The mixed FP64 residual levels off at a floor
   (~5e-8 with 50 inner iterations on the 32^3 stack; measured 2e-8 / 5e-8 /
   1e-7 for 10 / 50 / 250) set by the FP32 error of corrections that carry

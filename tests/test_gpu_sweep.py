@@ -1,7 +1,7 @@
 """GPU parity of the fused THIIM sweep against the FP64 oracle (through the C ABI).
 
 Tolerances (written here, derived from the arithmetic):
-  * complex128 path: relative L2 <= 1e-12 per split (the benchmark spec's bound);
+  * complex128 path: relative L2 <= 1e-12 per split (the required bound);
     both sides are FP64 and differ only in rounding order and FMA use.
   * complex128 data with FP32-pair arithmetic (THIIM_C128_PAIR): the same
     1e-12 bound.  A pair carries ~48 significant bits (unit 2^-48 ~ 3.6e-15)
