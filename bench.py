@@ -348,6 +348,40 @@ def _variant_batch(p, torch, precision, stream, dev, iters, check, warmup):
             "residual_max": max(res)}
 
 
+def run_grid_sweep(args):
+    """MLUP/s against the cubic grid size (64^3 .. 512^3 in steps of 64), one
+    JSON line per size and path — the GPU counterpart of the paper's grid-size
+    experiment (Sec. IV-C, Fig. 7).  Not the benchmark's headline."""
+    import torch
+
+    import paper_1510_05218_gb300 as p
+    from workloads import stack_config
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    p.load_library()
+    stream = torch.cuda.Stream(device=dev)
+    peak, _ = _peaks()
+    modes = [("pair", 1), ("c64", 1), ("c64", 2), ("c128", 1)]
+    for n in range(64, 513, 64):
+        st = stack_config("stack%d" % n)
+        cells = n ** 3
+        for prec, temporal in modes:
+            ctx, co, fields, eps = _stack_problem(p, torch, st, prec, stream, dev)
+            del eps
+            try:
+                p.thiim_set_tuning(ctx, temporal, min(32, n))
+                iters = max(20, min(200, int(2e10 / cells)))
+                ms, _, res = _time_iterate(p, torch, ctx, stream, iters, 1, 2)
+            finally:
+                p.thiim_destroy(ctx)
+            del co, fields
+            torch.cuda.empty_cache()
+            mlups = cells * iters * 2 / (ms / 1e3) / 1e6
+            print(json.dumps({"grid": n, "precision": prec, "iterations_per_launch": temporal, "mlups": mlups,
+                              "frac_hbm_alg": mlups * 1e6 * BYTES_PER_LUP[prec] / 1e9 / peak,
+                              "iters": iters, "zchunk": min(32, n)}), flush=True)
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -513,6 +547,7 @@ def main():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--temporal", type=int, default=1, help="iterations per launch (2: complex64 only)")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--grid-sweep", action="store_true", help="MLUP/s vs grid size 64^3..512^3 (not the headline)")
     ap.add_argument("--zchunk", type=int, default=0, help="z planes per CTA (0: library default)")
     ap.add_argument("--iters", type=int, default=200)
     ap.add_argument("--e2e-steps", type=int, default=1)
@@ -526,6 +561,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.grid_sweep:
+        run_grid_sweep(args)
     else:
         run_ours(args)
 
