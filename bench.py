@@ -33,6 +33,8 @@ if ROOT not in sys.path:
 
 METRIC = "THIIM E+H MLUP/s at 512^3 and % of HBM roofline; complex64 vs FP64 at ≤1e-6"
 BYTES_PER_LUP = {"c128": 52 * 16, "pair": 52 * 16, "c64": 52 * 8}   # 40 arrays read + 12 written per cell
+# material-table variant: 12 splits read + 12 written, one material-id byte
+TABLE_BYTES_PER_LUP = {"c128": 24 * 16 + 1, "pair": 24 * 16 + 1, "c64": 24 * 8 + 1}
 DTYPE = {"c128": "f64", "pair": "f32x2", "c64": "f32"}
 PRECISION_CODE = {"c128": 0, "c64": 1, "pair": 2}
 KERNEL = {"c128": "sweep_kernel<Native<double>>", "pair": "sweep_kernel<PairArith<1,1>>",
@@ -212,18 +214,28 @@ def _clock_index(local):
     return local if os.environ.get("CUDA_VISIBLE_DEVICES") is None else 0
 
 
-def _stack_problem(p, torch, st, precision, stream, dev):
-    """Context + device arrays of a layered stack, coefficients built on the GPU."""
+def _stack_problem(p, torch, st, precision, stream, dev, table=False):
+    """Context + device arrays of a layered stack, coefficients built on the GPU
+    (28 arrays, or with table=True a material map and (material, plane) table)."""
     prec = PRECISION_CODE[precision]
     dt = torch.complex64 if prec == p.THIIM_C64 else torch.complex128
     shape = (st.nz, st.ny, st.nx)
-    eps = torch.from_numpy(st.eps()).to(dev)
     ctx = p.thiim_create(st.nx, st.ny, st.nz, prec, 3, stream)
-    co = [torch.empty(shape, dtype=dt, device=dev) for _ in range(28)]
     fields = [torch.zeros(shape, dtype=dt, device=dev) for _ in range(12)]
-    with torch.cuda.stream(stream):
-        p.thiim_build_coeffs(ctx, eps, st.sigma_pml_e(), st.sigma_pml_h(), st.omega, st.tau, st.k_s, 1.0, co)
-    p.thiim_set_coeffs(ctx, co)
+    if table:
+        em = st.material_eps()
+        eps = torch.from_numpy(st.material_ids()).to(dev)     # the material map stands in for eps
+        co = [torch.empty(len(em) * st.nz * 28, dtype=dt, device=dev)]
+        with torch.cuda.stream(stream):
+            p.thiim_build_material_table(ctx, em, st.sigma_pml_e(), st.sigma_pml_h(), st.omega, st.tau, st.k_s,
+                                         1.0, co[0])
+        p.thiim_set_material_coeffs(ctx, eps, len(em), co[0])
+    else:
+        eps = torch.from_numpy(st.eps()).to(dev)
+        co = [torch.empty(shape, dtype=dt, device=dev) for _ in range(28)]
+        with torch.cuda.stream(stream):
+            p.thiim_build_coeffs(ctx, eps, st.sigma_pml_e(), st.sigma_pml_h(), st.omega, st.tau, st.k_s, 1.0, co)
+        p.thiim_set_coeffs(ctx, co)
     p.thiim_set_fields(ctx, fields)
     torch.cuda.synchronize()
     return ctx, co, fields, eps
@@ -249,9 +261,9 @@ def _time_iterate(p, torch, ctx, stream, iters, warmup, steps):
     return t0.elapsed_time(t1), sum(a.elapsed_time(b) for a, b in ev), res
 
 
-def _variant_sweep(p, torch, st, precision, stream, dev, iters, warmup, steps, peak, temporal=1, autotune=True):
-    ctx, co, fields, eps = _stack_problem(p, torch, st, precision, stream, dev)
-    del eps
+def _variant_sweep(p, torch, st, precision, stream, dev, iters, warmup, steps, peak, temporal=1, autotune=True,
+                   table=False):
+    ctx, co, fields, eps = _stack_problem(p, torch, st, precision, stream, dev, table=table)
     choice = None
     if temporal != 1:
         p.thiim_set_tuning(ctx, temporal, 0)
@@ -268,11 +280,17 @@ def _variant_sweep(p, torch, st, precision, stream, dev, iters, warmup, steps, p
         p.thiim_destroy(ctx)
     cells = st.nx * st.ny * st.nz
     launch_s = ms_iter / 1e3 / (steps * iters)
-    achieved = BYTES_PER_LUP[precision] * cells / launch_s / 1e9
-    del co, fields
+    alg = (TABLE_BYTES_PER_LUP if table else BYTES_PER_LUP)[precision]
+    achieved = alg * cells / launch_s / 1e9
+    del co, fields, eps
     torch.cuda.empty_cache()
+    kernel = KERNEL[precision] if temporal == 1 else "sweep2_kernel<Native<float>> (2 iterations/launch)"
+    if table:
+        kernel = kernel[:-1] + ", table>"
     return {"value": cells * iters * steps / (ms_total / 1e3) / 1e6, "unit": "MLUP/s", "dtype": DTYPE[precision],
-            "kernel": KERNEL[precision] if temporal == 1 else "sweep2_kernel<Native<float>> (2 iterations/launch)",
+            "kernel": kernel, "alg_bytes_per_lup": alg,
+            "coefficients": ("material map (1 B/cell) + (material, plane) table: a variant, not the paper's "
+                             "28-array layout" if table else "28 arrays"),
             "launch_ms": launch_s * 1e3 * temporal, "achieved_gbs": achieved,
             "frac_hbm": achieved / peak, "residual_last": res[-1], "steps": steps, "warmup": warmup,
             "iterations_per_launch": temporal, "tuning": list(choice) if choice else None,
@@ -491,6 +509,9 @@ def run_ours(args):
             if mode != args.precision:
                 variants[mode] = _variant_sweep(p, torch, st, mode, stream, dev, iters, 1, 1, peak)
         variants["c64_temporal2"] = _variant_sweep(p, torch, st, "c64", stream, dev, iters, 1, 1, peak, temporal=2)
+        for mode in ("pair", "c64"):
+            variants[mode + "_material_table"] = _variant_sweep(p, torch, st, mode, stream, dev, iters, 1, 1, peak,
+                                                               table=True)
         variants["mixed_c64_f64_defect"] = _variant_mixed(p, torch, st, stream, dev, 50, 4, 1)
         variants["batch32_" + args.precision] = _variant_batch(p, torch, args.precision, stream, dev, 200, 50, 1)
 

@@ -85,6 +85,8 @@ enum thiim_status {
 #define THIIM_N_COEFFS 28
 /* Longest segment thiim_adjoint_iterate recomputes from one checkpoint. */
 #define THIIM_MAX_ADJOINT_SEGMENT 64
+/* Materials a coefficient table may hold (the material id is one byte). */
+#define THIIM_MAX_MATERIALS 256
 
 /*
  * thiim_create — make a context for an nx * ny * nz grid.
@@ -186,6 +188,55 @@ int thiim_build_coeffs(thiim_ctx *ctx, const void *eps_r,
                        const double *sigma_pml_e, const double *sigma_pml_h,
                        double omega, double tau, int k_s, double amp_re,
                        double amp_im, void *const coeff[THIIM_N_COEFFS]);
+
+/*
+ * Compressed coefficients (a variant; the paper stores all 28 arrays, Sec.
+ * III, 40 complex values per cell in total).  In the workloads of Sec. I-A a
+ * cell's coefficients depend only on its material (eps_r) and its plane
+ * (absorbing-layer conductivity, source plane), so they can be kept as a
+ * table with one row of 28 per (material, plane) and a one-byte material id
+ * per cell: about 1 byte of coefficient data per cell instead of 28 complex
+ * values.  The sweep reads row (mat[p], k) where it would read element p of
+ * the 28 arrays; the arithmetic is otherwise the same, so a table built by
+ * thiim_build_material_table gives results bit-identical to the arrays that
+ * thiim_build_coeffs builds from the same materials.
+ *
+ * thiim_build_material_table — fill the table of n_mat materials.
+ *   n_mat:   1 .. THIIM_MAX_MATERIALS.
+ *   eps_mat: host array of 2 * n_mat doubles, (Re, Im) of each material's
+ *            relative permittivity, conventions as in thiim_build_coeffs.
+ *   the others as in thiim_build_coeffs.
+ *   table:   device array of n_mat * nz * 28 complex values in the context's
+ *            precision (complex64 for THIIM_C64, else complex128); entry
+ *            ci of row (m, k) is at table[(m * nz + k) * 28 + ci], ci in the
+ *            coefficient order of thiim_set_coeffs.  Owned by the caller.
+ * Synchronises the stream.  Errors: THIIM_ERR_ARG (as thiim_build_coeffs;
+ * also n_mat out of range or a zero or non-finite permittivity),
+ * THIIM_ERR_ALIGN, THIIM_ERR_NOMEM, THIIM_ERR_CUDA.
+ */
+int thiim_build_material_table(thiim_ctx *ctx, int n_mat, const double *eps_mat,
+                               const double *sigma_pml_e, const double *sigma_pml_h,
+                               double omega, double tau, int k_s, double amp_re,
+                               double amp_im, void *table);
+
+/*
+ * thiim_set_material_coeffs — borrow a material map and table in place of
+ * the 28 coefficient arrays; thiim_set_coeffs switches back.
+ *   mat:   device array of nx*ny*nz material ids (uint8, layout as the
+ *          fields), each below n_mat.  Ids are not checked on the device: an
+ *          id >= n_mat reads outside the table.
+ *   n_mat: rows of the table, 1 .. THIIM_MAX_MATERIALS.
+ *   table: device table as filled by thiim_build_material_table.
+ * thiim_iterate then runs one iteration per launch (thiim_set_tuning's
+ * temporal_block is ignored).  THIIM_C128_PAIR: the next thiim_iterate splits
+ * the table into FP32 pairs held by the library; call this function again
+ * after changing the table's contents.  thiim_mixed_solve,
+ * thiim_batch_iterate and thiim_adjoint_iterate need the 28 arrays and return
+ * THIIM_ERR_STATE for a context in this mode.  Errors: THIIM_ERR_ARG,
+ * THIIM_ERR_ALIGN.
+ */
+int thiim_set_material_coeffs(thiim_ctx *ctx, const unsigned char *mat, int n_mat,
+                              const void *table);
 
 /*
  * thiim_mixed_solve — complex64 sweeps with FP64 defect correction.

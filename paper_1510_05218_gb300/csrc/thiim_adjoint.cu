@@ -210,7 +210,7 @@ extern "C" int thiim_adjoint_iterate(thiim_ctx *c, void *const lambda[THIIM_N_FI
     if (!c || !lambda || !grad_coeff || !fwd_checkpoint || n_back < 1 || n_back > THIIM_MAX_ADJOINT_SEGMENT)
         return THIIM_ERR_ARG;
     if (c->precision != THIIM_C128) return THIIM_ERR_ARG;
-    if (!c->have_coeffs) return THIIM_ERR_STATE;
+    if (!c->have_coeffs || c->use_table) return THIIM_ERR_STATE;
     for (int i = 0; i < THIIM_N_FIELDS; ++i)
         if (!lambda[i] || !fwd_checkpoint[i] || !aligned(lambda[i], 16) || !aligned(fwd_checkpoint[i], 16))
             return lambda[i] && fwd_checkpoint[i] ? THIIM_ERR_ALIGN : THIIM_ERR_ARG;

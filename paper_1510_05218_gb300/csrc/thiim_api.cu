@@ -108,52 +108,122 @@ __device__ __forceinline__ void put(void *base, size_t i, dc v) {
     reinterpret_cast<V *>(base)[i] = w;
 }
 
+// The 28 coefficients of one cell: material eps (real part) and conductivity
+// sigma_mat = omega Im(eps_r), absorbing-layer conductivities of its planes.
+__device__ __forceinline__ void cell_coeffs(const BuildArgs &a, double eps, double sig_mat, int k, dc out[28]) {
+    const double wt = a.omega * a.tau;
+    const dc e_mh = cexpi(-0.5 * wt), e_ph = cexpi(0.5 * wt);
+    const dc e_m1 = cexpi(-wt), e_p1 = cexpi(wt);
+    for (int s = 0; s < 12; ++s) {
+        dc t, c;
+        if (s < 6) {             // H, Eq. 4 (mu = 1)
+            const double ss = along_z(s) ? a.sig_h[k] : 0.0;
+            const dc den = mk(e_ph.x + a.tau * ss, e_ph.y);
+            t = cdiv(e_mh, den);
+            c = cdiv(mk(a.tau, 0.0), den);
+        } else {
+            const double sg = sig_mat + (along_z(s) ? a.sig_e[k] : 0.0);
+            if (eps > 0.0) {     // Eq. 3
+                t = cdiv(e_m1, mk(1.0 + a.tau * sg / eps, 0.0));
+                c = cdiv(mk(a.tau * e_mh.x, a.tau * e_mh.y), mk(eps + a.tau * sg, 0.0));
+            } else {             // Eq. 5, back iteration
+                t = cdiv(e_p1, mk(1.0 - a.tau * sg / eps, 0.0));
+                c = cdiv(mk(-a.tau * e_ph.x, -a.tau * e_ph.y), mk(eps - a.tau * sg, 0.0));
+            }
+        }
+        out[T0 + s] = t;
+        out[C0 + s] = c;
+    }
+    out[SRC_HXY] = mk(0, 0);
+    out[SRC_EYX] = mk(0, 0);
+    out[SRC_HYX] = k == a.k_s ? cmul(out[C0 + HYX], a.src_h) : mk(0, 0);
+    out[SRC_EXY] = k == a.k_s ? cmul(out[C0 + EXY], a.src_e) : mk(0, 0);
+}
+
 template <typename V>
 __global__ void build_coeffs_kernel(const BuildArgs a) {
     const size_t n = (size_t)a.nx * a.ny * a.nz;
     const size_t plane = (size_t)a.nx * a.ny;
-    const double wt = a.omega * a.tau;
-    const dc e_mh = cexpi(-0.5 * wt), e_ph = cexpi(0.5 * wt);
-    const dc e_m1 = cexpi(-wt), e_p1 = cexpi(wt);
     for (size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (size_t)gridDim.x * blockDim.x) {
         const int k = (int)(p / plane);
         const double2 er = a.eps[p];
-        const double eps = er.x;
-        const double sig_mat = a.omega * er.y;
-        if (!(eps != 0.0) || !isfinite(eps) || !isfinite(er.y)) atomicOr(a.flag, 1);
-        dc c_hyx = mk(0, 0), c_exy = mk(0, 0);
-        for (int s = 0; s < 12; ++s) {
-            dc t, c;
-            if (s < 6) {             // H, Eq. 4 (mu = 1)
-                const double ss = along_z(s) ? a.sig_h[k] : 0.0;
-                const dc den = mk(e_ph.x + a.tau * ss, e_ph.y);
-                t = cdiv(e_mh, den);
-                c = cdiv(mk(a.tau, 0.0), den);
-            } else {
-                const double sg = sig_mat + (along_z(s) ? a.sig_e[k] : 0.0);
-                if (eps > 0.0) {     // Eq. 3
-                    t = cdiv(e_m1, mk(1.0 + a.tau * sg / eps, 0.0));
-                    c = cdiv(mk(a.tau * e_mh.x, a.tau * e_mh.y), mk(eps + a.tau * sg, 0.0));
-                } else {             // Eq. 5, back iteration
-                    t = cdiv(e_p1, mk(1.0 - a.tau * sg / eps, 0.0));
-                    c = cdiv(mk(-a.tau * e_ph.x, -a.tau * e_ph.y), mk(eps - a.tau * sg, 0.0));
-                }
-            }
-            put<V>(a.co[T0 + s], p, t);
-            put<V>(a.co[C0 + s], p, c);
-            if (s == HYX) c_hyx = c;
-            if (s == EXY) c_exy = c;
-        }
-        dc s_hyx = mk(0, 0), s_exy = mk(0, 0);
-        if (k == a.k_s) {
-            s_hyx = cmul(c_hyx, a.src_h);
-            s_exy = cmul(c_exy, a.src_e);
-        }
-        put<V>(a.co[SRC_HXY], p, mk(0, 0));
-        put<V>(a.co[SRC_HYX], p, s_hyx);
-        put<V>(a.co[SRC_EXY], p, s_exy);
-        put<V>(a.co[SRC_EYX], p, mk(0, 0));
+        if (!(er.x != 0.0) || !isfinite(er.x) || !isfinite(er.y)) atomicOr(a.flag, 1);
+        dc v[28];
+        cell_coeffs(a, er.x, a.omega * er.y, k, v);
+        for (int i = 0; i < 28; ++i) put<V>(a.co[i], p, v[i]);
     }
+}
+
+// Table of the compressed variant: row (m, k) holds the 28 coefficients of a
+// cell of material m on plane k.  a.eps holds the n_mat permittivities.
+template <typename V>
+__global__ void build_table_kernel(const BuildArgs a, int n_mat, void *table) {
+    const int rows = n_mat * a.nz;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += gridDim.x * blockDim.x) {
+        const int m = r / a.nz, k = r % a.nz;
+        const double2 er = a.eps[m];
+        if (!(er.x != 0.0) || !isfinite(er.x) || !isfinite(er.y)) atomicOr(a.flag, 1);
+        dc v[28];
+        cell_coeffs(a, er.x, a.omega * er.y, k, v);
+        for (int i = 0; i < 28; ++i) put<V>(table, (size_t)r * 28 + i, v[i]);
+    }
+}
+
+// Checks the builder's scalar arguments, uploads the absorbing-layer
+// conductivities and fills the scalar part of the builder's arguments.
+int prepare_build(thiim_ctx *c, const double *sigma_pml_e, const double *sigma_pml_h, double omega, double tau,
+                  int k_s, double amp_re, double amp_im, BuildArgs *out) {
+    if (!(tau > 0.0) || !isfinite(omega) || !isfinite(tau) || k_s >= c->nz) return THIIM_ERR_ARG;
+    // Discrete frequency of the fixed point and the incident wave number:
+    // omega_t = 2 sin(omega tau / 2) / tau, 2 sin(kappa / 2) = omega_t.
+    const double wt = 2.0 * sin(0.5 * omega * tau) / tau;
+    if (k_s >= 0 && !(fabs(wt) <= 2.0)) return THIIM_ERR_ARG;
+    if (!c->pml) {
+        if (cudaMalloc(&c->pml, 2 * (size_t)c->nz * sizeof(double)) != cudaSuccess) return THIIM_ERR_NOMEM;
+        if (cudaMalloc(&c->flag, sizeof(int)) != cudaSuccess) return THIIM_ERR_NOMEM;
+    }
+    double *host = (double *)calloc(2 * (size_t)c->nz, sizeof(double));
+    if (!host) return THIIM_ERR_NOMEM;
+    if (sigma_pml_e) memcpy(host, sigma_pml_e, (size_t)c->nz * sizeof(double));
+    if (sigma_pml_h) memcpy(host + c->nz, sigma_pml_h, (size_t)c->nz * sizeof(double));
+    cudaError_t e = cudaMemcpyAsync(c->pml, host, 2 * (size_t)c->nz * sizeof(double), cudaMemcpyHostToDevice,
+                                    c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->flag, 0, sizeof(int), c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);   // host buffer may go away
+    free(host);
+    if (e != cudaSuccess) return THIIM_ERR_CUDA;
+
+    BuildArgs &a = *out;
+    memset(&a, 0, sizeof(a));
+    a.sig_e = c->pml;
+    a.sig_h = c->pml + c->nz;
+    a.nx = c->nx; a.ny = c->ny; a.nz = c->nz;
+    a.omega = omega; a.tau = tau;
+    a.k_s = k_s;
+    a.flag = c->flag;
+    if (k_s >= 0) {
+        // Hyx (sign -1) at the scattered-field H plane k_s reads the incident
+        // E_x(k_s) = amp:  Src = +c_Hyx * amp.
+        // Exy (sign -1) at the total-field E plane k_s reads the incident
+        // H_y(k_s) = -(E_inc(k_s) - E_inc(k_s - 1)) / (i omega_t)
+        //          = -amp (1 - e^{i kappa}) / (i omega_t):  Src = +c_Exy * H_y.
+        const double kappa = 2.0 * asin(0.5 * wt);
+        const double dre = 1.0 - cos(kappa), dim = -sin(kappa);   // 1 - e^{i kappa}
+        const double nre = -(amp_re * dre - amp_im * dim), nim = -(amp_re * dim + amp_im * dre);
+        // divide by i omega_t:  (nre + i nim) / (i wt) = (nim - i nre) / wt
+        a.src_h.x = amp_re; a.src_h.y = amp_im;
+        a.src_e.x = nim / wt; a.src_e.y = -nre / wt;
+    }
+    return THIIM_OK;
+}
+
+// Waits for the builder and reports a zero or non-finite permittivity.
+int read_build_flag(thiim_ctx *c) {
+    int flag = 0;
+    if (cudaMemcpyAsync(&flag, c->flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess)
+        return THIIM_ERR_CUDA;
+    return flag ? THIIM_ERR_ARG : THIIM_OK;
 }
 
 }  // namespace
@@ -226,7 +296,20 @@ int thiim_set_coeffs(thiim_ctx *c, void *const coeff[THIIM_N_COEFFS]) {
     }
     memcpy(c->coeff, coeff, sizeof(c->coeff));
     c->have_coeffs = true;
+    c->use_table = false;
     c->pair_dirty = true;
+    return THIIM_OK;
+}
+
+int thiim_set_material_coeffs(thiim_ctx *c, const unsigned char *mat, int n_mat, const void *table) {
+    if (!c || !mat || !table || n_mat < 1 || n_mat > THIIM_MAX_MATERIALS) return THIIM_ERR_ARG;
+    if (!aligned(table, c->elem)) return THIIM_ERR_ALIGN;
+    c->mat = mat;
+    c->table = table;
+    c->n_mat = n_mat;
+    c->use_table = true;
+    c->have_coeffs = true;
+    c->pair_table_dirty = true;
     return THIIM_OK;
 }
 
@@ -265,7 +348,27 @@ int thiim_iterate(thiim_ctx *c, int n_iters) {
     if (!c->norms && cudaMalloc(&c->norms, 2 * sizeof(double)) != cudaSuccess) return THIIM_ERR_NOMEM;
 
     const bool pair = c->precision == THIIM_C128_PAIR;
-    if (pair) {
+    const bool tbl = c->use_table;
+    if (pair && tbl) {
+        const size_t n = (size_t)c->n_mat * c->nz * THIIM_N_COEFFS;
+        if (c->pair_table_cap < n) {
+            if (c->pair_table) cudaFree(c->pair_table);
+            c->pair_table = nullptr;
+            c->pair_table_cap = 0;
+            if (cudaMalloc(&c->pair_table, n * 16) != cudaSuccess) {
+                cudaGetLastError();
+                return THIIM_ERR_NOMEM;
+            }
+            c->pair_table_cap = n;
+            c->pair_table_dirty = true;
+        }
+        if (c->pair_table_dirty) {
+            const void *src = c->table;
+            void *dst = c->pair_table;
+            if (split_coeffs(&src, &dst, 1, n, c->stream) != cudaSuccess) return THIIM_ERR_CUDA;
+            c->pair_table_dirty = false;
+        }
+    } else if (pair) {
         if (!c->pair_co[0]) {
             for (int i = 0; i < THIIM_N_COEFFS; ++i) {
                 if (cudaMalloc(&c->pair_co[i], c->n_cells * 16) != cudaSuccess) {
@@ -291,15 +394,26 @@ int thiim_iterate(thiim_ctx *c, int n_iters) {
     a.bc = c->bc;
     a.zchunk = c->zchunk;
     a.tiles_x = tx;
+    if (tbl) {
+        a.mat = c->mat;
+        a.table = pair ? c->pair_table : c->table;
+    }
     void **from = c->user, **to = c->alt;
     for (int it = 0; it < n_iters;) {
         // temporal blocking: two iterations per launch while two remain
-        const int step = (c->temporal == 2 && n_iters - it >= 2) ? 2 : 1;
+        // (array coefficients only; the table variant runs one per launch)
+        const int step = (c->temporal == 2 && !tbl && n_iters - it >= 2) ? 2 : 1;
         memcpy(a.src, from, sizeof(a.src));
         memcpy(a.dst, to, sizeof(a.dst));
         a.partials = (it + step == n_iters) ? c->partials : nullptr;
         cudaError_t e;
-        if (pair)   // intermediate iterates stay as float4 pairs; first reads and last writes complex128
+        if (tbl && pair)
+            e = launch_sweep_pair_tbl(a, grid, c->stream, it > 0, it < n_iters - 1);
+        else if (tbl && c->precision == THIIM_C128)
+            e = launch_sweep_f64_tbl(a, grid, c->stream);
+        else if (tbl)
+            e = launch_sweep_f32_tbl(a, grid, c->stream);
+        else if (pair)   // intermediate iterates stay as float4 pairs; first reads and last writes complex128
             e = launch_sweep_pair(a, grid, c->stream, it > 0, it < n_iters - 1);
         else if (c->precision == THIIM_C128)
             e = launch_sweep_f64(a, grid, c->stream);
@@ -339,54 +453,16 @@ int thiim_build_coeffs(thiim_ctx *c, const void *eps_r, const double *sigma_pml_
                        const double *sigma_pml_h, double omega, double tau, int k_s, double amp_re,
                        double amp_im, void *const coeff[THIIM_N_COEFFS]) {
     if (!c || !eps_r || !coeff) return THIIM_ERR_ARG;
-    if (!(tau > 0.0) || !isfinite(omega) || !isfinite(tau) || k_s >= c->nz) return THIIM_ERR_ARG;
     if (!aligned(eps_r, 16)) return THIIM_ERR_ALIGN;
     for (int i = 0; i < THIIM_N_COEFFS; ++i) {
         if (!coeff[i]) return THIIM_ERR_ARG;
         if (!aligned(coeff[i], c->elem)) return THIIM_ERR_ALIGN;
     }
-    // Discrete frequency of the fixed point and the incident wave number:
-    // omega_t = 2 sin(omega tau / 2) / tau, 2 sin(kappa / 2) = omega_t.
-    const double wt = 2.0 * sin(0.5 * omega * tau) / tau;
-    if (k_s >= 0 && !(fabs(wt) <= 2.0)) return THIIM_ERR_ARG;
-    if (!c->pml) {
-        if (cudaMalloc(&c->pml, 2 * (size_t)c->nz * sizeof(double)) != cudaSuccess) return THIIM_ERR_NOMEM;
-        if (cudaMalloc(&c->flag, sizeof(int)) != cudaSuccess) return THIIM_ERR_NOMEM;
-    }
-    double *host = (double *)calloc(2 * (size_t)c->nz, sizeof(double));
-    if (!host) return THIIM_ERR_NOMEM;
-    if (sigma_pml_e) memcpy(host, sigma_pml_e, (size_t)c->nz * sizeof(double));
-    if (sigma_pml_h) memcpy(host + c->nz, sigma_pml_h, (size_t)c->nz * sizeof(double));
-    cudaError_t e = cudaMemcpyAsync(c->pml, host, 2 * (size_t)c->nz * sizeof(double), cudaMemcpyHostToDevice,
-                                    c->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(c->flag, 0, sizeof(int), c->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);   // host buffer may go away
-    free(host);
-    if (e != cudaSuccess) return THIIM_ERR_CUDA;
-
     BuildArgs a;
-    memset(&a, 0, sizeof(a));
+    int st = prepare_build(c, sigma_pml_e, sigma_pml_h, omega, tau, k_s, amp_re, amp_im, &a);
+    if (st) return st;
     a.eps = (const double2 *)eps_r;
-    a.sig_e = c->pml;
-    a.sig_h = c->pml + c->nz;
     memcpy(a.co, coeff, sizeof(a.co));
-    a.nx = c->nx; a.ny = c->ny; a.nz = c->nz;
-    a.omega = omega; a.tau = tau;
-    a.k_s = k_s;
-    a.flag = c->flag;
-    if (k_s >= 0) {
-        // Hyx (sign -1) at the scattered-field H plane k_s reads the incident
-        // E_x(k_s) = amp:  Src = +c_Hyx * amp.
-        // Exy (sign -1) at the total-field E plane k_s reads the incident
-        // H_y(k_s) = -(E_inc(k_s) - E_inc(k_s - 1)) / (i omega_t)
-        //          = -amp (1 - e^{i kappa}) / (i omega_t):  Src = +c_Exy * H_y.
-        const double kappa = 2.0 * asin(0.5 * wt);
-        const double dre = 1.0 - cos(kappa), dim = -sin(kappa);   // 1 - e^{i kappa}
-        const double nre = -(amp_re * dre - amp_im * dim), nim = -(amp_re * dim + amp_im * dre);
-        // divide by i omega_t:  (nre + i nim) / (i wt) = (nim - i nre) / wt
-        a.src_h.x = amp_re; a.src_h.y = amp_im;
-        a.src_e.x = nim / wt; a.src_e.y = -nre / wt;
-    }
     const int threads = 256;
     long blocks = (long)((c->n_cells + threads - 1) / threads);
     if (blocks > 32L * c->num_sms) blocks = 32L * c->num_sms;
@@ -396,11 +472,38 @@ int thiim_build_coeffs(thiim_ctx *c, const void *eps_r, const double *sigma_pml_
     else
         build_coeffs_kernel<float2><<<(unsigned)blocks, threads, 0, c->stream>>>(a);
     if (cudaGetLastError() != cudaSuccess) return THIIM_ERR_CUDA;
-    int flag = 0;
-    if (cudaMemcpyAsync(&flag, c->flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+    return read_build_flag(c);
+}
+
+int thiim_build_material_table(thiim_ctx *c, int n_mat, const double *eps_mat, const double *sigma_pml_e,
+                               const double *sigma_pml_h, double omega, double tau, int k_s, double amp_re,
+                               double amp_im, void *table) {
+    if (!c || !eps_mat || !table || n_mat < 1 || n_mat > THIIM_MAX_MATERIALS) return THIIM_ERR_ARG;
+    if (!aligned(table, c->elem)) return THIIM_ERR_ALIGN;
+    for (int m = 0; m < 2 * n_mat; ++m)
+        if (!isfinite(eps_mat[m])) return THIIM_ERR_ARG;
+    for (int m = 0; m < n_mat; ++m)
+        if (eps_mat[2 * m] == 0.0) return THIIM_ERR_ARG;
+    BuildArgs a;
+    int st = prepare_build(c, sigma_pml_e, sigma_pml_h, omega, tau, k_s, amp_re, amp_im, &a);
+    if (st) return st;
+    if (!c->mat_eps && cudaMalloc(&c->mat_eps, 2 * THIIM_MAX_MATERIALS * sizeof(double)) != cudaSuccess)
+        return THIIM_ERR_NOMEM;
+    if (cudaMemcpyAsync(c->mat_eps, eps_mat, 2 * (size_t)n_mat * sizeof(double), cudaMemcpyHostToDevice,
+                        c->stream) != cudaSuccess ||
         cudaStreamSynchronize(c->stream) != cudaSuccess)
         return THIIM_ERR_CUDA;
-    return flag ? THIIM_ERR_ARG : THIIM_OK;
+    a.eps = (const double2 *)c->mat_eps;
+    const int threads = 256;
+    const int rows = n_mat * c->nz;
+    const int blocks = (rows + threads - 1) / threads;
+    c->pair_table_dirty = true;
+    if (c->precision != THIIM_C64)
+        build_table_kernel<double2><<<blocks, threads, 0, c->stream>>>(a, n_mat, table);
+    else
+        build_table_kernel<float2><<<blocks, threads, 0, c->stream>>>(a, n_mat, table);
+    if (cudaGetLastError() != cudaSuccess) return THIIM_ERR_CUDA;
+    return read_build_flag(c);
 }
 
 void thiim_destroy(thiim_ctx *c) {
@@ -417,6 +520,8 @@ void thiim_destroy(thiim_ctx *c) {
     for (int m = 0; m < THIIM_MAX_ADJOINT_SEGMENT; ++m)
         for (int i = 0; i < THIIM_N_FIELDS; ++i)
             if (c->adj_states[m][i]) cudaFree(c->adj_states[m][i]);
+    if (c->pair_table) cudaFree(c->pair_table);
+    if (c->mat_eps) cudaFree(c->mat_eps);
     if (c->partials) cudaFree(c->partials);
     if (c->norms) cudaFree(c->norms);
     if (c->pml) cudaFree(c->pml);

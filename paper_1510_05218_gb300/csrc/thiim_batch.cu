@@ -172,7 +172,7 @@ extern "C" int thiim_batch_iterate(thiim_ctx *const ctx[], int nb, int max_iters
     const int prec = ctx[0] ? ctx[0]->precision : -1;
     for (int b = 0; b < nb; ++b) {
         if (!ctx[b] || ctx[b]->precision != prec || ctx[b]->device != ctx[0]->device) return THIIM_ERR_ARG;
-        if (!ctx[b]->have_fields || !ctx[b]->have_coeffs) return THIIM_ERR_STATE;
+        if (!ctx[b]->have_fields || !ctx[b]->have_coeffs || ctx[b]->use_table) return THIIM_ERR_STATE;
     }
     cudaStream_t s = ctx[0]->stream;
     const bool pair = prec == THIIM_C128_PAIR;

@@ -22,6 +22,15 @@ struct thiim_ctx {
     void *alt[THIIM_N_FIELDS];   // library's second field set
     void *pair_co[THIIM_N_COEFFS];  // THIIM_C128_PAIR: coefficients split into float4 pairs
     bool pair_dirty;             // coefficients changed since they were last split
+    // material-table coefficients (thiim_set_material_coeffs)
+    bool use_table;              // the sweep reads table rows selected by mat[] instead of coeff[]
+    const unsigned char *mat;    // per-cell material id
+    const void *table;           // n_mat * nz * 28 complex values, context precision
+    int n_mat;
+    void *pair_table;            // THIIM_C128_PAIR: the table split into float4 pairs
+    size_t pair_table_cap;       // entries allocated in pair_table
+    bool pair_table_dirty;       // table set or rebuilt since it was last split
+    double *mat_eps;             // device: 2 * THIIM_MAX_MATERIALS, the table builder's permittivities
     bool have_coeffs, have_fields, have_norm;
     int zchunk;                  // planes per CTA of the sweep
     int temporal;                // iterations per launch: 1, or 2 (temporal blocking, THIIM_C64)

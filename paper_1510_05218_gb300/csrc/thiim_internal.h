@@ -32,6 +32,12 @@ cudaError_t launch_sweep_f32(const SweepArgs &a, dim3 grid, cudaStream_t s);
 // float4 pairs (see split_coeffs).
 cudaError_t launch_sweep_pair(const SweepArgs &a, dim3 grid, cudaStream_t s, bool in_pairs, bool out_pairs);
 
+// The same sweeps reading coefficients from the (material, plane) table
+// (a.mat, a.table); pair coefficients are float4 pairs of the table.
+cudaError_t launch_sweep_f64_tbl(const SweepArgs &a, dim3 grid, cudaStream_t s);
+cudaError_t launch_sweep_f32_tbl(const SweepArgs &a, dim3 grid, cudaStream_t s);
+cudaError_t launch_sweep_pair_tbl(const SweepArgs &a, dim3 grid, cudaStream_t s, bool in_pairs, bool out_pairs);
+
 // Defect-correction sweeps: FP64 defect r = F(x) - x written as complex64,
 // and the complex64 correction iteration delta <- M delta + r (a.xsrc = r).
 cudaError_t launch_defect_f64(const SweepArgs &a, dim3 grid, cudaStream_t s);

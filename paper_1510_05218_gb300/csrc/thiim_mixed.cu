@@ -66,7 +66,7 @@ extern "C" int thiim_mixed_solve(thiim_ctx *c, void *const coeff64[THIIM_N_COEFF
                                  double *rel_residual) {
     if (!c || !coeff64 || !x64 || inner_iters < 1 || max_outer < 0) return THIIM_ERR_ARG;
     if (c->precision != THIIM_C64) return THIIM_ERR_ARG;
-    if (!c->have_fields || !c->have_coeffs) return THIIM_ERR_STATE;
+    if (!c->have_fields || !c->have_coeffs || c->use_table) return THIIM_ERR_STATE;
     for (int i = 0; i < THIIM_N_COEFFS; ++i) {
         if (!coeff64[i]) return THIIM_ERR_ARG;
         if (!aligned(coeff64[i], 16)) return THIIM_ERR_ALIGN;

@@ -42,6 +42,23 @@ struct SweepArgs {
     int tiles_x;           // CTAs along x
     double *partials;      // 2 doubles per CTA (|dF|^2, |F|^2) or nullptr
     const void *xsrc[12];  // SWEEP_CORRECT: per-split source arrays replacing Src
+    // Material-table coefficients (the compressed variant): coefficient ci of
+    // cell p on plane k is table[(mat[p] * nz + k) * 28 + ci].
+    const unsigned char *mat;
+    const void *table;
+};
+
+// Where the coefficients of one cell come from: element p of each of the 28
+// arrays, or one 28-entry row of the (material, plane) table.
+template <typename A, bool TBL>
+struct CoefAt {
+    size_t base;
+    __device__ __forceinline__ CoefAt(const SweepArgs &a, size_t p, int k) {
+        base = TBL ? ((size_t)a.mat[p] * a.nz + k) * 28 : p;
+    }
+    __device__ __forceinline__ typename A::Z get(const SweepArgs &a, int ci) const {
+        return TBL ? A::ld_coef(a.table, base + ci) : A::ld_coef(a.co[ci], base);
+    }
 };
 
 // Sweep modes.
@@ -84,14 +101,15 @@ __device__ __forceinline__ double dnorm2(typename A::Z a, typename A::Z b) {
     return x * x + y * y;
 }
 
-template <typename A, int MODE>
+template <typename A, int MODE, bool TBL = false>
 struct SplitIO {
     typedef typename A::Z Z;
     // t x + c d (+ Src if the split has a source array; none in SWEEP_CORRECT).
     // The result feeds the full-field sums that the E update reads.
-    __device__ static __forceinline__ Z update(const SweepArgs &a, int s, int src_coef, size_t p, Z x, Z d) {
-        const Z t = A::ld_coef(a.co[T0 + s], p), c = A::ld_coef(a.co[C0 + s], p);
-        if (MODE != SWEEP_CORRECT && src_coef >= 0) return A::upd_src(x, t, c, d, A::ld_coef(a.co[src_coef], p));
+    __device__ static __forceinline__ Z update(const SweepArgs &a, int s, int src_coef, const CoefAt<A, TBL> &cr,
+                                               Z x, Z d) {
+        const Z t = cr.get(a, T0 + s), c = cr.get(a, C0 + s);
+        if (MODE != SWEEP_CORRECT && src_coef >= 0) return A::upd_src(x, t, c, d, cr.get(a, src_coef));
         return A::upd(x, t, c, d);
     }
     // Store splits s and s+1 (the two parts of one component).
@@ -129,10 +147,10 @@ struct SplitIO {
 // chunk `chunk`.  partial_out (2 doubles) receives the CTA's |dF|^2, |F|^2
 // when non-null.  Used by the per-problem kernel below and by the batched
 // persistent kernel (thiim_batch.cu).
-template <typename A, int TX, int TY, int NT, int MODE>
+template <typename A, int TX, int TY, int NT, int MODE, bool TBL = false>
 __device__ __forceinline__ void sweep_tile(const SweepArgs &a, int tile, int chunk, double *partial_out) {
     typedef typename A::Z Z;
-    typedef SplitIO<A, MODE> IO;
+    typedef SplitIO<A, MODE, TBL> IO;
     constexpr int EW = TX + 2, EH = TY + 2;   // E^n region: -1 .. TX (x), -1 .. TY (y)
     constexpr int HW = TX + 1, HH = TY + 1;   // new-H region: 0 .. TX, 0 .. TY
     __shared__ Vec3<Z> sE[2][EH][EW];         // full E^n at planes k (cur) and k-1
@@ -205,12 +223,13 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, int tile, int chu
                 const Z oxy = A::ld_field(a.src[HXY], p), oxz = A::ld_field(a.src[HXZ], p);
                 const Z oyx = A::ld_field(a.src[HYX], p), oyz = A::ld_field(a.src[HYZ], p);
                 const Z ozx = A::ld_field(a.src[HZX], p), ozy = A::ld_field(a.src[HZY], p);
-                const Z nxy = IO::update(a, HXY, SRC_HXY, p, oxy, dHxy);
-                const Z nxz = IO::update(a, HXZ, -1, p, oxz, dHxz);
-                const Z nyx = IO::update(a, HYX, SRC_HYX, p, oyx, dHyx);
-                const Z nyz = IO::update(a, HYZ, -1, p, oyz, dHyz);
-                const Z nzx = IO::update(a, HZX, -1, p, ozx, dHzx);
-                const Z nzy = IO::update(a, HZY, -1, p, ozy, dHzy);
+                const CoefAt<A, TBL> cr(a, p, kk);
+                const Z nxy = IO::update(a, HXY, SRC_HXY, cr, oxy, dHxy);
+                const Z nxz = IO::update(a, HXZ, -1, cr, oxz, dHxz);
+                const Z nyx = IO::update(a, HYX, SRC_HYX, cr, oyx, dHyx);
+                const Z nyz = IO::update(a, HYZ, -1, cr, oyz, dHyz);
+                const Z nzx = IO::update(a, HZX, -1, cr, ozx, dHzx);
+                const Z nzy = IO::update(a, HZY, -1, cr, ozy, dHzy);
                 hn.x = A::add(nxy, nxz);
                 hn.y = A::add(nyx, nyz);
                 hn.z = A::add(nzx, nzy);
@@ -250,12 +269,13 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, int tile, int chu
                 const Z oxy = A::ld_field(a.src[EXY], p), oxz = A::ld_field(a.src[EXZ], p);
                 const Z oyx = A::ld_field(a.src[EYX], p), oyz = A::ld_field(a.src[EYZ], p);
                 const Z ozx = A::ld_field(a.src[EZX], p), ozy = A::ld_field(a.src[EZY], p);
-                const Z nxy = IO::update(a, EXY, SRC_EXY, p, oxy, dExy);
-                const Z nxz = IO::update(a, EXZ, -1, p, oxz, dExz);
-                const Z nyx = IO::update(a, EYX, SRC_EYX, p, oyx, dEyx);
-                const Z nyz = IO::update(a, EYZ, -1, p, oyz, dEyz);
-                const Z nzx = IO::update(a, EZX, -1, p, ozx, dEzx);
-                const Z nzy = IO::update(a, EZY, -1, p, ozy, dEzy);
+                const CoefAt<A, TBL> cr(a, p, ke);
+                const Z nxy = IO::update(a, EXY, SRC_EXY, cr, oxy, dExy);
+                const Z nxz = IO::update(a, EXZ, -1, cr, oxz, dExz);
+                const Z nyx = IO::update(a, EYX, SRC_EYX, cr, oyx, dEyx);
+                const Z nyz = IO::update(a, EYZ, -1, cr, oyz, dEyz);
+                const Z nzx = IO::update(a, EZX, -1, cr, ozx, dEzx);
+                const Z nzy = IO::update(a, EZY, -1, cr, ozy, dEzy);
                 IO::store_pair(a, EXY, p, nxy, oxy, nxz, oxz);
                 IO::store_pair(a, EYX, p, nyx, oyx, nyz, oyz);
                 IO::store_pair(a, EZX, p, nzx, ozx, nzy, ozy);
@@ -288,11 +308,11 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, int tile, int chu
     }
 }
 
-template <typename A, int TX, int TY, int NT, int MINB, int MODE = SWEEP_PLAIN>
+template <typename A, int TX, int TY, int NT, int MINB, int MODE = SWEEP_PLAIN, bool TBL = false>
 __global__ void __launch_bounds__(NT, (MINB > 0 ? MINB : (NT == 256 ? A::min_blocks : 1)))
 sweep_kernel(const SweepArgs a) {
     const size_t cta = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
-    sweep_tile<A, TX, TY, NT, MODE>(a, blockIdx.x, blockIdx.y, a.partials ? a.partials + 2 * cta : nullptr);
+    sweep_tile<A, TX, TY, NT, MODE, TBL>(a, blockIdx.x, blockIdx.y, a.partials ? a.partials + 2 * cta : nullptr);
 }
 
 }  // namespace thiim

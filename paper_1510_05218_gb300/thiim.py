@@ -18,6 +18,7 @@ THIIM_C128_PAIR = 2
 THIIM_PERIODIC_X = 1
 THIIM_PERIODIC_Y = 2
 THIIM_PERIODIC_Z = 4
+THIIM_MAX_MATERIALS = 256
 
 _HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "thiim.h")
 _lib = None
@@ -76,6 +77,11 @@ def load_library(build_if_missing: bool = False):
     lib.thiim_build_coeffs_grad.argtypes = [vp, vp, vp, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                             ctypes.c_double, ctypes.c_double, P28, vp]
     lib.thiim_build_coeffs_grad.restype = ctypes.c_int
+    lib.thiim_build_material_table.argtypes = [vp, ctypes.c_int, vp, vp, vp, ctypes.c_double, ctypes.c_double,
+                                               ctypes.c_int, ctypes.c_double, ctypes.c_double, vp]
+    lib.thiim_build_material_table.restype = ctypes.c_int
+    lib.thiim_set_material_coeffs.argtypes = [vp, vp, ctypes.c_int, vp]
+    lib.thiim_set_material_coeffs.restype = ctypes.c_int
     lib.thiim_destroy.argtypes = [vp]
     lib.thiim_destroy.restype = None
     lib.thiim_strerror.argtypes = [ctypes.c_int]
@@ -175,6 +181,33 @@ def thiim_build_coeffs(ctx, eps_r, sigma_pml_e, sigma_pml_h, omega, tau, k_s, am
         float(omega), float(tau), int(k_s), amp.real, amp.imag, _ptrs(coeffs, 28, "coefficient")))
 
 
+def _dev_ptr(t, what):
+    if not (t.is_cuda and t.is_contiguous()):
+        raise ValueError("%s must be a contiguous CUDA tensor" % what)
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def thiim_build_material_table(ctx, eps_mat, sigma_pml_e, sigma_pml_h, omega, tau, k_s, amp, table):
+    """Fill `table` (CUDA tensor of n_mat * nz * 28 complex values) for the permittivities eps_mat."""
+    import numpy as np
+    em = np.asarray(eps_mat, dtype=np.complex128).ravel()
+    eh = np.ascontiguousarray(np.stack([em.real, em.imag], 1).ravel())
+    se = None if sigma_pml_e is None else np.ascontiguousarray(sigma_pml_e, dtype=np.float64)
+    sh = None if sigma_pml_h is None else np.ascontiguousarray(sigma_pml_h, dtype=np.float64)
+    amp = complex(amp)
+    _check("thiim_build_material_table", load_library().thiim_build_material_table(
+        ctx, len(em), eh.ctypes.data_as(ctypes.c_void_p),
+        None if se is None else se.ctypes.data_as(ctypes.c_void_p),
+        None if sh is None else sh.ctypes.data_as(ctypes.c_void_p),
+        float(omega), float(tau), int(k_s), amp.real, amp.imag, _dev_ptr(table, "table")))
+
+
+def thiim_set_material_coeffs(ctx, mat, n_mat, table):
+    """Use the uint8 material map `mat` and the table in place of the 28 coefficient arrays."""
+    _check("thiim_set_material_coeffs", load_library().thiim_set_material_coeffs(
+        ctx, _dev_ptr(mat, "mat"), int(n_mat), _dev_ptr(table, "table")))
+
+
 def thiim_mixed_solve(ctx, coeffs64, x64, inner_iters=50, max_outer=1, tol=0.0):
     """Defect-correction solve; returns (corrections applied, last FP64 residual)."""
     done = ctypes.c_int()
@@ -272,6 +305,18 @@ class Solver:
         coeffs = self.coeffs if self.coeffs is not None else self._empty(28)
         thiim_build_coeffs(self.ctx, eps_r, sigma_pml_e, sigma_pml_h, omega, tau, k_s, amp, coeffs)
         self.set_coeffs(coeffs)
+
+    def set_material_coeffs(self, mat, table, n_mat):
+        """Material-table coefficients; the tensors are kept alive here."""
+        self.mat, self.table = mat, table
+        thiim_set_material_coeffs(self.ctx, mat, n_mat, table)
+
+    def build_material_table(self, eps_mat, sigma_pml_e, sigma_pml_h, omega, tau, k_s, amp=1.0):
+        """A new table for the permittivities eps_mat (one per material id)."""
+        import torch
+        table = torch.empty(len(eps_mat) * self.nz * 28, dtype=self.dtype, device=self.device)
+        thiim_build_material_table(self.ctx, eps_mat, sigma_pml_e, sigma_pml_h, omega, tau, k_s, amp, table)
+        return table
 
     def iterate(self, n):
         thiim_iterate(self.ctx, n)

@@ -141,6 +141,29 @@ class LayeredStack:
     def eps(self) -> np.ndarray:
         return self.eps_planes(0, self.nz)
 
+    # material order of the ids below
+    MATERIAL_ORDER = ("air", "asi", "glass", "ag")
+
+    def material_eps(self) -> np.ndarray:
+        """Permittivity of material id m = 0..3 (order MATERIAL_ORDER)."""
+        return np.array([self.material(n) for n in self.MATERIAL_ORDER], np.complex128)
+
+    def material_id_planes(self, k0: int, k1: int) -> np.ndarray:
+        """Material id (uint8) of cells k0 <= k < k1; material_eps()[ids] == eps_planes(k0, k1)."""
+        zt = self.z_top()
+        out = np.zeros((k1 - k0, self.ny, self.nx), np.uint8)
+        for idx, k in enumerate(range(k0, k1)):
+            if k >= self.z_glass_end:
+                out[idx] = 3
+            elif k >= self.z_asi_end:
+                out[idx] = 2
+            else:
+                out[idx][k >= zt] = 1
+        return out
+
+    def material_ids(self) -> np.ndarray:
+        return self.material_id_planes(0, self.nz)
+
     def absorber_mask(self) -> np.ndarray:
         """Cells of the a-Si:H-like absorber (bool, shape (nz, ny, nx))."""
         zt = self.z_top()
