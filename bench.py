@@ -424,7 +424,8 @@ def run_ours(args):
     stream = torch.cuda.Stream(device=dev)
     peak, peak_kind = _peaks()
 
-    ctx, co, fields, eps = _stack_problem(p, torch, st, args.precision, stream, dev)
+    table = args.coeffs == "table"
+    ctx, co, fields, eps = _stack_problem(p, torch, st, args.precision, stream, dev, table=table)
     tuning_info = None
     if args.temporal != 1 or args.zchunk:
         p.thiim_set_tuning(ctx, args.temporal, args.zchunk)
@@ -461,16 +462,16 @@ def run_ours(args):
 
     # roofline of the dominant kernel (the fused sweep): one launch per iteration
     launch_s = ms_iter_calls / 1e3 / (args.steps * iters)
-    alg_bytes = BYTES_PER_LUP[args.precision] * cells
-    achieved = alg_bytes / launch_s / 1e9
-    kernel_key = KERNEL[args.precision]
+    alg_per_lup = (TABLE_BYTES_PER_LUP if table else BYTES_PER_LUP)[args.precision]
+    achieved = alg_per_lup * cells / launch_s / 1e9
+    kernel_key = KERNEL[args.precision][:-1] + ", table>" if table else KERNEL[args.precision]
     traffic = _traffic(kernel_key, cells)
 
     # --- end to end through the public API with host buffers --------------
     e2e = None
     if not args.no_e2e:
         host_fields = [torch.empty(shape, dtype=dt).pin_memory() for _ in range(12)]
-        h2d = eps_pinned.numel() * 16 + 2 * st.nz * 8
+        h2d = eps_pinned.numel() * eps_pinned.element_size() + 2 * st.nz * 8
         d2h = sum(t.numel() * t.element_size() for t in host_fields)
         e2e_times = []
         for s in range(args.e2e_warmup + args.e2e_steps):
@@ -478,8 +479,13 @@ def run_ours(args):
             barrier()
             t0 = time.perf_counter()
             with torch.cuda.stream(stream):
-                eps.copy_(eps_pinned, non_blocking=True)
-                p.thiim_build_coeffs(ctx, eps, sig_e, sig_h, st.omega, st.tau, st.k_s, 1.0, co)
+                eps.copy_(eps_pinned, non_blocking=True)       # permittivity map, or material ids
+                if table:
+                    p.thiim_build_material_table(ctx, st.material_eps(), sig_e, sig_h, st.omega, st.tau, st.k_s,
+                                                 1.0, co[0])
+                    p.thiim_set_material_coeffs(ctx, eps, len(st.material_eps()), co[0])
+                else:
+                    p.thiim_build_coeffs(ctx, eps, sig_e, sig_h, st.omega, st.tau, st.k_s, 1.0, co)
                 for f in fields:
                     f.zero_()
             p.thiim_set_fields(ctx, fields)
@@ -495,8 +501,9 @@ def run_ours(args):
         e2e = {"value": world * cells * iters / statistics.median(e2e_times) / 1e6, "unit": "MLUP/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                "steps": args.e2e_steps,
-               "what": "H2D permittivity map, thiim_build_coeffs, zero fields, thiim_iterate(%d), "
-                       "thiim_residual, D2H of the 12 fields" % iters}
+               "what": ("H2D material-id map, thiim_build_material_table" if table else
+                        "H2D permittivity map, thiim_build_coeffs") +
+                       ", zero fields, thiim_iterate(%d), thiim_residual, D2H of the 12 fields" % iters}
         del host_fields
 
     p.thiim_destroy(ctx)
@@ -536,12 +543,14 @@ def run_ours(args):
                                    args.workload, st.nx, st.ny, st.nz, PRECISION_NOTE[args.precision], iters),
                    "grid": [st.nx, st.ny, st.nz], "iters_per_step": iters, "precision": args.precision,
                    "kernel": "fused out-of-place z-streaming sweep, one launch per iteration",
+                   "coefficients": ("material-id map (1 B/cell) + (material, plane) table: a variant, not the "
+                                    "paper's 28-array layout" if table else "28 arrays (the paper's layout)"),
                    "tuning": tuning_info,
                    "l2": "inputs larger than L2 (no flush needed)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                     "kernel": kernel_key, "alg_bytes_per_lup": BYTES_PER_LUP[args.precision],
+                     "kernel": kernel_key, "alg_bytes_per_lup": alg_per_lup,
                      "launch_ms": launch_s * 1e3},
         "gflops_paper_count": value * FLOPS_PER_LUP / 1e3,
         "residual_last": residuals[-1] if residuals else None,
@@ -566,6 +575,8 @@ def main():
     ap.add_argument("--workload", default="stack512")
     ap.add_argument("--precision", default="pair", choices=["c128", "pair", "c64"])
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--coeffs", default="arrays", choices=["arrays", "table"],
+                    help="table: material-id map + (material, plane) table (a variant, not the headline layout)")
     ap.add_argument("--temporal", type=int, default=1, help="iterations per launch (2: complex64 only)")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--grid-sweep", action="store_true", help="MLUP/s vs grid size 64^3..512^3 (not the headline)")
