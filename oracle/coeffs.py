@@ -23,8 +23,8 @@ as e^{+i omega t}); the splits whose difference runs along z (Hxy, Hyx, Exy,
 Eyx) also carry the absorbing-layer conductivity of their z position (E at k,
 H at k - 1/2).  mu = 1; sig*_mat is zero unless given.
 
-Plane-wave source (total-field/scattered-field plane at k_s, x polarised,
-normal incidence): the incident wave solves the discrete equations in air,
+Plane-wave source (total-field/scattered-field plane at k_s, normal
+incidence): the incident wave solves the discrete equations in air,
 E_x(k) = A e(-kappa (k - k_s)) with 2 sin(kappa/2) = omega_t, where
 omega_t = 2 sin(omega tau / 2) / tau is the discrete frequency that the fixed
 point of Eqs. 3-4 carries, and H_y(k) = -(E_x(k) - E_x(k-1)) / (i omega_t).
@@ -33,6 +33,11 @@ field, so H_yx(k_s) reads the incident E_x(k_s) across the plane and
 E_xy(k_s) reads the incident H_y(k_s):
   SrcHyx(k_s) = -sign(Hyx) c_Hyx(k_s) E_inc(k_s),
   SrcExy(k_s) = -sign(Exy) c_Exy(k_s) H_inc(k_s).
+The y-polarised wave (E_y, H_x) follows from the same curl with the other
+two z-difference splits: H_x(k) = +(E_y(k) - E_y(k-1)) / (i omega_t), and
+  SrcHxy(k_s) = -sign(Hxy) c_Hxy(k_s) E_y,inc(k_s),
+  SrcEyx(k_s) = -sign(Eyx) c_Eyx(k_s) H_x,inc(k_s).
+A general polarisation (Jones vector (A_x, A_y)) is the sum of the two.
 """
 from __future__ import annotations
 
@@ -50,16 +55,18 @@ def discrete_omega(omega: float, tau: float) -> float:
     return 2.0 * math.sin(omega * tau / 2.0) / tau
 
 
-def incident_wave(omega: float, tau: float, k_s: int, amp: complex = 1.0):
-    """(E_inc(k), H_inc(k)) callables of the discrete x-polarised plane wave in air."""
+def incident_wave(omega: float, tau: float, k_s: int, amp: complex = 1.0, pol: str = "x"):
+    """(E_inc(k), H_inc(k)) callables of the discrete plane wave in air:
+    pol "x": (E_x, H_y), H_y = -dE/(i omega_t); pol "y": (E_y, H_x), H_x = +dE/(i omega_t)."""
     wt = discrete_omega(omega, tau)
     kappa = 2.0 * math.asin(wt / 2.0)
+    sgn = -1.0 if pol == "x" else 1.0
 
     def e_inc(k):
         return amp * np.exp(-1j * kappa * (np.asarray(k, dtype=np.float64) - k_s))
 
     def h_inc(k):
-        return -(e_inc(k) - e_inc(np.asarray(k) - 1)) / (1j * wt)
+        return sgn * (e_inc(k) - e_inc(np.asarray(k) - 1)) / (1j * wt)
 
     return e_inc, h_inc
 
@@ -69,7 +76,8 @@ def build_coeffs(eps_r, sigma_pml_e, sigma_pml_h, omega, tau, tfsf=None, S=None,
 
     eps_r: (nz, ny, nx) complex relative permittivity per cell (physics convention).
     sigma_pml_e / sigma_pml_h: (nz,) absorbing conductivity at E / H planes.
-    tfsf: optional (k_s, amplitude) of the plane-wave source.
+    tfsf: optional (k_s, amplitude) of the x-polarised plane-wave source, or
+       (k_s, A_x, A_y) for a general polarisation (Jones vector).
     S: optional dict {"Hxy"|"Hyx"|"Exy"|"Eyx": array} of physical sources
        S_H / S_E of Eqs. 3-5 on the four source splits.
     sigma_star: optional (nz, ny, nx) magnetic conductivity of the material
@@ -114,17 +122,27 @@ def build_coeffs(eps_r, sigma_pml_e, sigma_pml_h, omega, tau, tfsf=None, S=None,
             s = SPLITS.index(name)
             srcs[name] = srcs[name] + src_scale[s] * np.asarray(arr, np.complex128)
     if tfsf is not None:
-        k_s, amp = tfsf
-        e_inc, h_inc = incident_wave(omega, tau, k_s, amp)
-        s_h = SPLITS.index("Hyx")
-        s_e = SPLITS.index("Exy")
-        sign_h = rule(s_h)[3]
-        sign_e = rule(s_e)[3]
-        srcs["Hyx"][k_s] += -sign_h * c[s_h][k_s] * e_inc(k_s)
-        srcs["Exy"][k_s] += -sign_e * c[s_e][k_s] * h_inc(k_s)
+        k_s = tfsf[0]
+        amps = {"x": tfsf[1], "y": tfsf[2] if len(tfsf) > 2 else 0.0}
+        for pol, h_name, e_name in (("x", "Hyx", "Exy"), ("y", "Hxy", "Eyx")):
+            if amps[pol] == 0:
+                continue
+            e_inc, h_inc = incident_wave(omega, tau, k_s, amps[pol], pol)
+            s_h = SPLITS.index(h_name)
+            s_e = SPLITS.index(e_name)
+            sign_h = rule(s_h)[3]
+            sign_e = rule(s_e)[3]
+            srcs[h_name][k_s] += -sign_h * c[s_h][k_s] * e_inc(k_s)
+            srcs[e_name][k_s] += -sign_e * c[s_e][k_s] * h_inc(k_s)
     out = [np.ascontiguousarray(np.broadcast_to(a, (nz, ny, nx)).astype(np.complex128)) for a in t + c]
     out += [srcs[n] for n in ("Hxy", "Hyx", "Exy", "Eyx")]
     return out
+
+
+def absorbed_power(fields, sigma):
+    """1/2 sum over cells of sigma |E|^2, E = the full E components (split sums)."""
+    e2 = sum(np.abs(fields[2 * a] + fields[2 * a + 1]) ** 2 for a in (3, 4, 5))
+    return 0.5 * float(np.sum(np.asarray(sigma, np.float64) * e2))
 
 
 def stack_coeffs(stack):
