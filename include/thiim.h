@@ -190,6 +190,38 @@ int thiim_build_coeffs(thiim_ctx *ctx, const void *eps_r,
                        double amp_im, void *const coeff[THIIM_N_COEFFS]);
 
 /*
+ * thiim_build_coeffs_jones — thiim_build_coeffs for a normally incident wave
+ * of any polarisation.  The paper covers a solar cell's spectrum with 80-160
+ * runs (Sec. V); an unpolarised spectrum averages the x- and y-polarised
+ * runs.  jones: host array {Re A_x, Im A_x, Re A_y, Im A_y}, the incident
+ * E = (A_x, A_y, 0) at plane k_s.  The y component (E_y, H_x = +dE_y/(i
+ * omega_t)) enters through the two Src arrays the x-polarised wave leaves
+ * zero: SrcHxy(k_s) = -c_Hxy A_y, SrcEyx(k_s) = -c_Eyx H_x,inc(k_s).
+ * thiim_build_coeffs(..., amp_re, amp_im, ...) equals jones = {amp_re,
+ * amp_im, 0, 0}.  Errors as thiim_build_coeffs, plus THIIM_ERR_ARG for a
+ * NULL or non-finite jones.
+ */
+int thiim_build_coeffs_jones(thiim_ctx *ctx, const void *eps_r,
+                             const double *sigma_pml_e, const double *sigma_pml_h,
+                             double omega, double tau, int k_s, const double jones[4],
+                             void *const coeff[THIIM_N_COEFFS]);
+
+/*
+ * thiim_absorbed_power — P = 1/2 sum over cells of sigma |E|^2 for the
+ * context's current fields (E = the full components, split sums), summed in
+ * FP64 in a fixed order (deterministic).  Divided by the incident power of
+ * the plane wave it is the absorption of a solar cell at one wavelength and
+ * polarisation, the quantity of the paper's spectrum runs (Sec. V).
+ *   sigma: device array of nx*ny*nz conductivities (layout as the fields),
+ *          e.g. omega Im(eps_r) on the absorbing layer and 0 elsewhere.
+ *   power: host double receiving P.
+ * Synchronises the stream.  Errors: THIIM_ERR_ARG (NULL), THIIM_ERR_ALIGN
+ * (sigma not 8-byte aligned), THIIM_ERR_STATE (no fields set),
+ * THIIM_ERR_NONFINITE, THIIM_ERR_NOMEM, THIIM_ERR_CUDA.
+ */
+int thiim_absorbed_power(thiim_ctx *ctx, const double *sigma, double *power);
+
+/*
  * Compressed coefficients (a variant; the paper stores all 28 arrays, Sec.
  * III, 40 complex values per cell in total).  In the workloads of Sec. I-A a
  * cell's coefficients depend only on its material (eps_r) and its plane
@@ -205,6 +237,8 @@ int thiim_build_coeffs(thiim_ctx *ctx, const void *eps_r,
  *   n_mat:   1 .. THIIM_MAX_MATERIALS.
  *   eps_mat: host array of 2 * n_mat doubles, (Re, Im) of each material's
  *            relative permittivity, conventions as in thiim_build_coeffs.
+ *   jones:   host array {Re A_x, Im A_x, Re A_y, Im A_y} of the plane wave
+ *            (as in thiim_build_coeffs_jones).
  *   the others as in thiim_build_coeffs.
  *   table:   device array of n_mat * nz * 28 complex values in the context's
  *            precision (complex64 for THIIM_C64, else complex128); entry
@@ -216,8 +250,8 @@ int thiim_build_coeffs(thiim_ctx *ctx, const void *eps_r,
  */
 int thiim_build_material_table(thiim_ctx *ctx, int n_mat, const double *eps_mat,
                                const double *sigma_pml_e, const double *sigma_pml_h,
-                               double omega, double tau, int k_s, double amp_re,
-                               double amp_im, void *table);
+                               double omega, double tau, int k_s, const double jones[4],
+                               void *table);
 
 /*
  * thiim_set_material_coeffs — borrow a material map and table in place of
@@ -300,7 +334,9 @@ int thiim_adjoint_iterate(thiim_ctx *ctx, void *const lambda[THIIM_N_FIELDS],
  * hence the material conductivity fixed.  Only the six E splits' t and c (and
  * SrcExy at the source plane) depend on the permittivity (Eqs. 3 and 5).
  * The other arguments are those given to thiim_build_coeffs (sigma_pml_h is
- * not needed).  Enqueued on the context's stream.
+ * not needed); the source term is that of its x-polarised wave (the y part
+ * of thiim_build_coeffs_jones, SrcEyx, is not differentiated here).
+ * Enqueued on the context's stream.
  * Errors: THIIM_ERR_ARG, THIIM_ERR_ALIGN, THIIM_ERR_NOMEM, THIIM_ERR_CUDA.
  */
 int thiim_build_coeffs_grad(thiim_ctx *ctx, const void *eps_r, const double *sigma_pml_e,

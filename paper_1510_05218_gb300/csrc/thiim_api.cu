@@ -92,8 +92,11 @@ struct BuildArgs {
     int nx, ny, nz;
     double omega, tau;
     int k_s;                  // -1: no source
-    dc src_h;                 // factor of c_Hyx at k_s
+    dc src_h;                 // factor of c_Hyx at k_s (x polarisation)
     dc src_e;                 // factor of c_Exy at k_s
+    bool pol_y;               // the wave has a y component:
+    dc src_hxy;               // factor of c_Hxy at k_s
+    dc src_eyx;               // factor of c_Eyx at k_s
     int *flag;
 };
 
@@ -134,8 +137,8 @@ __device__ __forceinline__ void cell_coeffs(const BuildArgs &a, double eps, doub
         out[T0 + s] = t;
         out[C0 + s] = c;
     }
-    out[SRC_HXY] = mk(0, 0);
-    out[SRC_EYX] = mk(0, 0);
+    out[SRC_HXY] = (a.pol_y && k == a.k_s) ? cmul(out[C0 + HXY], a.src_hxy) : mk(0, 0);
+    out[SRC_EYX] = (a.pol_y && k == a.k_s) ? cmul(out[C0 + EYX], a.src_eyx) : mk(0, 0);
     out[SRC_HYX] = k == a.k_s ? cmul(out[C0 + HYX], a.src_h) : mk(0, 0);
     out[SRC_EXY] = k == a.k_s ? cmul(out[C0 + EXY], a.src_e) : mk(0, 0);
 }
@@ -172,8 +175,10 @@ __global__ void build_table_kernel(const BuildArgs a, int n_mat, void *table) {
 // Checks the builder's scalar arguments, uploads the absorbing-layer
 // conductivities and fills the scalar part of the builder's arguments.
 int prepare_build(thiim_ctx *c, const double *sigma_pml_e, const double *sigma_pml_h, double omega, double tau,
-                  int k_s, double amp_re, double amp_im, BuildArgs *out) {
+                  int k_s, const double jones[4], BuildArgs *out) {
     if (!(tau > 0.0) || !isfinite(omega) || !isfinite(tau) || k_s >= c->nz) return THIIM_ERR_ARG;
+    for (int i = 0; i < 4; ++i)
+        if (!isfinite(jones[i])) return THIIM_ERR_ARG;
     // Discrete frequency of the fixed point and the incident wave number:
     // omega_t = 2 sin(omega tau / 2) / tau, 2 sin(kappa / 2) = omega_t.
     const double wt = 2.0 * sin(0.5 * omega * tau) / tau;
@@ -203,16 +208,24 @@ int prepare_build(thiim_ctx *c, const double *sigma_pml_e, const double *sigma_p
     a.flag = c->flag;
     if (k_s >= 0) {
         // Hyx (sign -1) at the scattered-field H plane k_s reads the incident
-        // E_x(k_s) = amp:  Src = +c_Hyx * amp.
+        // E_x(k_s) = A_x:  Src = +c_Hyx * A_x.
         // Exy (sign -1) at the total-field E plane k_s reads the incident
         // H_y(k_s) = -(E_inc(k_s) - E_inc(k_s - 1)) / (i omega_t)
-        //          = -amp (1 - e^{i kappa}) / (i omega_t):  Src = +c_Exy * H_y.
+        //          = -A_x (1 - e^{i kappa}) / (i omega_t):  Src = +c_Exy * H_y.
+        // The y component (E_y, H_x = +dE_y / (i omega_t)) enters through
+        // Hxy and Eyx (sign +1):  Src = -c_Hxy * A_y, Src = -c_Eyx * H_x.
         const double kappa = 2.0 * asin(0.5 * wt);
         const double dre = 1.0 - cos(kappa), dim = -sin(kappa);   // 1 - e^{i kappa}
-        const double nre = -(amp_re * dre - amp_im * dim), nim = -(amp_re * dim + amp_im * dre);
-        // divide by i omega_t:  (nre + i nim) / (i wt) = (nim - i nre) / wt
-        a.src_h.x = amp_re; a.src_h.y = amp_im;
-        a.src_e.x = nim / wt; a.src_e.y = -nre / wt;
+        // -A (1 - e^{i kappa}) / (i omega_t); (n_re + i n_im) / (i wt) = (n_im - i n_re) / wt
+        auto h_factor = [&](double are, double aim, dc *f) {
+            const double nre = -(are * dre - aim * dim), nim = -(are * dim + aim * dre);
+            f->x = nim / wt; f->y = -nre / wt;
+        };
+        a.src_h.x = jones[0]; a.src_h.y = jones[1];
+        h_factor(jones[0], jones[1], &a.src_e);
+        a.pol_y = jones[2] != 0.0 || jones[3] != 0.0;
+        a.src_hxy.x = -jones[2]; a.src_hxy.y = -jones[3];
+        h_factor(jones[2], jones[3], &a.src_eyx);   // -H_x = -A_y (1 - e^{i kappa}) / (i omega_t)
     }
     return THIIM_OK;
 }
@@ -452,14 +465,21 @@ int thiim_residual(thiim_ctx *c, double *rel_residual) {
 int thiim_build_coeffs(thiim_ctx *c, const void *eps_r, const double *sigma_pml_e,
                        const double *sigma_pml_h, double omega, double tau, int k_s, double amp_re,
                        double amp_im, void *const coeff[THIIM_N_COEFFS]) {
-    if (!c || !eps_r || !coeff) return THIIM_ERR_ARG;
+    const double jones[4] = {amp_re, amp_im, 0.0, 0.0};
+    return thiim_build_coeffs_jones(c, eps_r, sigma_pml_e, sigma_pml_h, omega, tau, k_s, jones, coeff);
+}
+
+int thiim_build_coeffs_jones(thiim_ctx *c, const void *eps_r, const double *sigma_pml_e,
+                             const double *sigma_pml_h, double omega, double tau, int k_s,
+                             const double jones[4], void *const coeff[THIIM_N_COEFFS]) {
+    if (!c || !eps_r || !coeff || !jones) return THIIM_ERR_ARG;
     if (!aligned(eps_r, 16)) return THIIM_ERR_ALIGN;
     for (int i = 0; i < THIIM_N_COEFFS; ++i) {
         if (!coeff[i]) return THIIM_ERR_ARG;
         if (!aligned(coeff[i], c->elem)) return THIIM_ERR_ALIGN;
     }
     BuildArgs a;
-    int st = prepare_build(c, sigma_pml_e, sigma_pml_h, omega, tau, k_s, amp_re, amp_im, &a);
+    int st = prepare_build(c, sigma_pml_e, sigma_pml_h, omega, tau, k_s, jones, &a);
     if (st) return st;
     a.eps = (const double2 *)eps_r;
     memcpy(a.co, coeff, sizeof(a.co));
@@ -476,16 +496,16 @@ int thiim_build_coeffs(thiim_ctx *c, const void *eps_r, const double *sigma_pml_
 }
 
 int thiim_build_material_table(thiim_ctx *c, int n_mat, const double *eps_mat, const double *sigma_pml_e,
-                               const double *sigma_pml_h, double omega, double tau, int k_s, double amp_re,
-                               double amp_im, void *table) {
-    if (!c || !eps_mat || !table || n_mat < 1 || n_mat > THIIM_MAX_MATERIALS) return THIIM_ERR_ARG;
+                               const double *sigma_pml_h, double omega, double tau, int k_s,
+                               const double jones[4], void *table) {
+    if (!c || !eps_mat || !table || !jones || n_mat < 1 || n_mat > THIIM_MAX_MATERIALS) return THIIM_ERR_ARG;
     if (!aligned(table, c->elem)) return THIIM_ERR_ALIGN;
     for (int m = 0; m < 2 * n_mat; ++m)
         if (!isfinite(eps_mat[m])) return THIIM_ERR_ARG;
     for (int m = 0; m < n_mat; ++m)
         if (eps_mat[2 * m] == 0.0) return THIIM_ERR_ARG;
     BuildArgs a;
-    int st = prepare_build(c, sigma_pml_e, sigma_pml_h, omega, tau, k_s, amp_re, amp_im, &a);
+    int st = prepare_build(c, sigma_pml_e, sigma_pml_h, omega, tau, k_s, jones, &a);
     if (st) return st;
     if (!c->mat_eps && cudaMalloc(&c->mat_eps, 2 * THIIM_MAX_MATERIALS * sizeof(double)) != cudaSuccess)
         return THIIM_ERR_NOMEM;
@@ -524,6 +544,7 @@ void thiim_destroy(thiim_ctx *c) {
     if (c->mat_eps) cudaFree(c->mat_eps);
     if (c->partials) cudaFree(c->partials);
     if (c->norms) cudaFree(c->norms);
+    if (c->power) cudaFree(c->power);
     if (c->pml) cudaFree(c->pml);
     if (c->flag) cudaFree(c->flag);
     delete c;

@@ -37,6 +37,7 @@ struct thiim_ctx {
     double *partials;            // 2 doubles per sweep CTA
     size_t partials_cap;         // in CTAs
     double *norms;               // device: |dF|^2, |F|^2 of the last iteration
+    double *power;               // device: 2 doubles, thiim_absorbed_power's result
     double *pml;                 // device: 2*nz absorbing-layer conductivities
     int *flag;                   // device: error flag of the coefficient builder
     // defect-correction state (thiim_mixed_solve)

@@ -78,7 +78,12 @@ def load_library(build_if_missing: bool = False):
                                             ctypes.c_double, ctypes.c_double, P28, vp]
     lib.thiim_build_coeffs_grad.restype = ctypes.c_int
     lib.thiim_build_material_table.argtypes = [vp, ctypes.c_int, vp, vp, vp, ctypes.c_double, ctypes.c_double,
-                                               ctypes.c_int, ctypes.c_double, ctypes.c_double, vp]
+                                               ctypes.c_int, vp, vp]
+    lib.thiim_build_coeffs_jones.argtypes = [vp, vp, vp, vp, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                             vp, P28]
+    lib.thiim_build_coeffs_jones.restype = ctypes.c_int
+    lib.thiim_absorbed_power.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_double)]
+    lib.thiim_absorbed_power.restype = ctypes.c_int
     lib.thiim_build_material_table.restype = ctypes.c_int
     lib.thiim_set_material_coeffs.argtypes = [vp, vp, ctypes.c_int, vp]
     lib.thiim_set_material_coeffs.restype = ctypes.c_int
@@ -181,25 +186,53 @@ def thiim_build_coeffs(ctx, eps_r, sigma_pml_e, sigma_pml_h, omega, tau, k_s, am
         float(omega), float(tau), int(k_s), amp.real, amp.imag, _ptrs(coeffs, 28, "coefficient")))
 
 
+def _jones(amp_x, amp_y):
+    ax, ay = complex(amp_x), complex(amp_y)
+    return (ctypes.c_double * 4)(ax.real, ax.imag, ay.real, ay.imag)
+
+
+def _host_profile(a):
+    import numpy as np
+    if a is None:
+        return None, None
+    arr = np.ascontiguousarray(a, dtype=np.float64)
+    return arr, arr.ctypes.data_as(ctypes.c_void_p)
+
+
+def thiim_build_coeffs_jones(ctx, eps_r, sigma_pml_e, sigma_pml_h, omega, tau, k_s, amp_x, amp_y, coeffs):
+    """thiim_build_coeffs for the incident wave E = (amp_x, amp_y, 0)."""
+    se, se_p = _host_profile(sigma_pml_e)
+    sh, sh_p = _host_profile(sigma_pml_h)
+    _check("thiim_build_coeffs_jones", load_library().thiim_build_coeffs_jones(
+        ctx, _dev_ptr(eps_r, "eps_r"), se_p, sh_p, float(omega), float(tau), int(k_s), _jones(amp_x, amp_y),
+        _ptrs(coeffs, 28, "coefficient")))
+
+
+def thiim_absorbed_power(ctx, sigma) -> float:
+    """1/2 sum sigma |E|^2 over the context's current fields (sigma: float64 CUDA tensor)."""
+    out = ctypes.c_double()
+    _check("thiim_absorbed_power", load_library().thiim_absorbed_power(ctx, _dev_ptr(sigma, "sigma"),
+                                                                       ctypes.byref(out)))
+    return out.value
+
+
 def _dev_ptr(t, what):
     if not (t.is_cuda and t.is_contiguous()):
         raise ValueError("%s must be a contiguous CUDA tensor" % what)
     return ctypes.c_void_p(t.data_ptr())
 
 
-def thiim_build_material_table(ctx, eps_mat, sigma_pml_e, sigma_pml_h, omega, tau, k_s, amp, table):
-    """Fill `table` (CUDA tensor of n_mat * nz * 28 complex values) for the permittivities eps_mat."""
+def thiim_build_material_table(ctx, eps_mat, sigma_pml_e, sigma_pml_h, omega, tau, k_s, amp, table, amp_y=0.0):
+    """Fill `table` (CUDA tensor of n_mat * nz * 28 complex values) for the permittivities eps_mat;
+    the plane wave is E = (amp, amp_y, 0)."""
     import numpy as np
     em = np.asarray(eps_mat, dtype=np.complex128).ravel()
     eh = np.ascontiguousarray(np.stack([em.real, em.imag], 1).ravel())
-    se = None if sigma_pml_e is None else np.ascontiguousarray(sigma_pml_e, dtype=np.float64)
-    sh = None if sigma_pml_h is None else np.ascontiguousarray(sigma_pml_h, dtype=np.float64)
-    amp = complex(amp)
+    se, se_p = _host_profile(sigma_pml_e)
+    sh, sh_p = _host_profile(sigma_pml_h)
     _check("thiim_build_material_table", load_library().thiim_build_material_table(
-        ctx, len(em), eh.ctypes.data_as(ctypes.c_void_p),
-        None if se is None else se.ctypes.data_as(ctypes.c_void_p),
-        None if sh is None else sh.ctypes.data_as(ctypes.c_void_p),
-        float(omega), float(tau), int(k_s), amp.real, amp.imag, _dev_ptr(table, "table")))
+        ctx, len(em), eh.ctypes.data_as(ctypes.c_void_p), se_p, sh_p,
+        float(omega), float(tau), int(k_s), _jones(amp, amp_y), _dev_ptr(table, "table")))
 
 
 def thiim_set_material_coeffs(ctx, mat, n_mat, table):
