@@ -9,8 +9,11 @@ links or executes anything here, and nothing here imports the product.
 * ``coeffs.py``       the per-cell coefficient arrays t, c and the source
   arrays derived from Eqs. 3-5, in NumPy FP64.
   ``thiim_oracle.c`` also holds the adjoint of one iteration (reverse mode)
-  with the coefficient gradients; ``coeffs.py`` the derivatives of the
-  coefficients with respect to the real permittivity.
+  with the coefficient gradients (``adjoint_steady`` sums it at a fixed
+  point); ``coeffs.py`` the derivatives of the coefficients with respect to
+  the real permittivity and the absorbed power.
 """
-from .thiim_oracle import iterate, adjoint_step, rule, SPLITS, FIELD_INDEX, COEFF_NAMES  # noqa: F401
-from .coeffs import build_coeffs, coeff_eps_derivatives, incident_wave, discrete_omega  # noqa: F401
+from .thiim_oracle import (iterate, adjoint_step, adjoint_steady, rule, SPLITS, FIELD_INDEX,  # noqa: F401
+                           COEFF_NAMES)
+from .coeffs import (build_coeffs, coeff_eps_derivatives, incident_wave, discrete_omega,  # noqa: F401
+                     absorbed_power)

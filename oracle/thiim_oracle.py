@@ -85,3 +85,33 @@ def adjoint_step(lam, grad, x_n, x_np1, coeffs, bc: int = 3) -> None:
                                  _ptrs(x_np1, shape), _ptrs(coeffs, shape))
     if rc != 0:
         raise ValueError("oracle_adjoint_step failed (%d)" % rc)
+
+
+def adjoint_steady(g, x_star, coeffs, bc: int = 3, max_iters: int = 100000, tol: float = 0.0):
+    """Steady-state adjoint at a fixed point x* = F(x*) of the iteration.
+
+    The gradient of J(x*) with respect to the coefficients is (dF/da)^H lam*
+    where lam* = M^H lam* + g solves the adjoint fixed point (M the linear
+    part of one iteration, g the gradient of J with respect to conj(x*)).
+    Written as the reverse iteration of adjoint_step with every state equal
+    to x*: lam* = sum_k (M^H)^k g and the gradient is the sum of the per-step
+    contributions.  Terms are added until max_iters have been summed or the
+    last one is <= tol times the sum (norms over all 12 arrays).
+    Returns (lam*, grad (28 arrays), terms summed, |last term| / |lam*|).
+    """
+    shape = g[0].shape
+    lam = [np.array(a, np.complex128) for a in g]
+    total = [np.zeros(shape, np.complex128) for _ in range(12)]
+    grad = [np.zeros(shape, np.complex128) for _ in range(28)]
+    k, rel = 0, float("inf")
+    while k < max_iters:
+        term = np.sqrt(sum(float(np.vdot(a, a).real) for a in lam))
+        for s, a in zip(total, lam):
+            s += a
+        adjoint_step(lam, grad, x_star, x_star, coeffs, bc)
+        k += 1
+        tot = np.sqrt(sum(float(np.vdot(a, a).real) for a in total))
+        rel = term / tot if tot > 0 else 0.0
+        if tol > 0 and rel <= tol:
+            break
+    return total, grad, k, rel
