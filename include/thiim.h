@@ -326,6 +326,41 @@ int thiim_adjoint_iterate(thiim_ctx *ctx, void *const lambda[THIIM_N_FIELDS],
                           const void *const fwd_checkpoint[THIIM_N_FIELDS], int n_back);
 
 /*
+ * thiim_adjoint_steady — reverse-mode gradient of an objective of the
+ * CONVERGED solution (not in the paper; inverse design of the converged
+ * absorption).  At a fixed point x* = F(x*) of the iteration the gradient of
+ * J(x*) with respect to the coefficients is (dF/da)^H lam*, where the
+ * adjoint field lam* = M^H lam* + g solves the adjoint fixed point (M the
+ * linear part of one iteration, g the gradient of J with respect to conj(x*)
+ * in torch's convention).  lam* = sum_k (M^H)^k g is summed term by term with
+ * the reverse iteration of thiim_adjoint_iterate (without gradient work per
+ * term), and the coefficient gradient is evaluated once, on lam*.
+ *   ctx:         a THIIM_C128 context with its 28 coefficient arrays set.
+ *   lambda:      12 device arrays; in: g; out: lam* (the terms summed).
+ *   grad_coeff:  28 device arrays; the gradient is ADDED to them.
+ *   x_star:      12 device arrays, the converged iterate (read only).
+ *   max_iters:   maximum number of terms (>= 1; 1 gives the one-term sum g).
+ *   check_every: terms between convergence checks (>= 1; each synchronises).
+ *   tol:         stop once |last term| <= tol |lam*| (norms over the 12
+ *                arrays); 0 sums exactly max_iters terms.
+ *   iters_out, rel_out: optional; terms summed, |last term| / |lam*|.
+ * Convergence: the iteration has modes that never decay where sigma* = 0
+ * (split differences and curl-free H rotate with |t| = 1); sources never
+ * excite them, so the forward solve converges, but a seed g with an
+ * antisymmetric part on an E split pair, or a curl-free part on H, feeds
+ * them and the sum does not converge (rel_out stays large).  An objective
+ * of the full E components (g equal on the two splits of each E component,
+ * zero on H), such as the absorbed power, never does.  Scratch: 18 complex128 arrays of the grid
+ * (shared with thiim_adjoint_iterate).  Synchronises the stream.
+ * Errors: THIIM_ERR_ARG, THIIM_ERR_ALIGN, THIIM_ERR_STATE, THIIM_ERR_NOMEM,
+ * THIIM_ERR_NONFINITE, THIIM_ERR_CUDA.
+ */
+int thiim_adjoint_steady(thiim_ctx *ctx, void *const lambda[THIIM_N_FIELDS],
+                         void *const grad_coeff[THIIM_N_COEFFS],
+                         const void *const x_star[THIIM_N_FIELDS], int max_iters, int check_every,
+                         double tol, int *iters_out, double *rel_out);
+
+/*
  * thiim_build_coeffs_grad — chain rule through thiim_build_coeffs: given the
  * gradients G_a of a real objective with respect to the 28 complex128
  * coefficient arrays (torch's complex convention, 2 dJ/dconj(a)), write

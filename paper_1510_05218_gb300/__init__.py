@@ -10,7 +10,7 @@ from .thiim import (  # noqa: F401
     THIIM_MAX_MATERIALS,
     ThiimError, lib_path, load_library, exported_symbols, declared_symbols,
     thiim_create, thiim_set_stream, thiim_set_tuning, thiim_set_coeffs, thiim_set_fields, thiim_iterate,
-    thiim_residual, thiim_build_coeffs, thiim_mixed_solve, thiim_batch_iterate, thiim_adjoint_iterate, thiim_build_coeffs_grad,
+    thiim_residual, thiim_build_coeffs, thiim_mixed_solve, thiim_batch_iterate, thiim_adjoint_iterate, thiim_adjoint_steady, thiim_build_coeffs_grad,
     thiim_build_material_table, thiim_set_material_coeffs, thiim_build_coeffs_jones, thiim_absorbed_power,
     thiim_step_noalloc, thiim_destroy, thiim_strerror, thiim_version,
     Solver,

@@ -7,7 +7,10 @@ thiim_build_coeffs_grad (d objective / d Re eps per cell, Im eps held fixed).
 fields (thiim_iterate) and keeps every `every`-th iterate as a checkpoint; its
 backward replays each segment from its checkpoint and reverses it with
 thiim_adjoint_iterate, so memory holds N/every checkpoints plus one segment.
-Both run entirely in libthiim.so kernels; torch only owns the tensors.
+``solve_steady(coeffs, tol)`` iterates until the residual reaches tol; its
+backward is the steady-state adjoint (thiim_adjoint_steady), the gradient of
+the converged solution, with no checkpoints.
+All run entirely in libthiim.so kernels; torch only owns the tensors.
 Gradients follow torch's complex convention (2 dJ/dconj(z) for complex z).
 """
 from __future__ import annotations
@@ -66,6 +69,35 @@ class _Solve(torch.autograd.Function):
         return (None, None, None, *gco)
 
 
+class _SolveSteady(torch.autograd.Function):
+    @staticmethod
+    def forward(fctx, ctx, tol, max_iters, check_every, adj_tol, *coeffs):
+        co = [c.detach().contiguous() for c in coeffs]
+        T.thiim_set_coeffs(ctx, co)
+        x = [torch.zeros_like(co[0]) for _ in range(12)]
+        T.thiim_set_fields(ctx, x)
+        done, res = 0, float("inf")
+        while done < max_iters and not res <= tol:
+            n = min(check_every, max_iters - done)
+            T.thiim_iterate(ctx, n)
+            done += n
+            res = T.thiim_residual(ctx)
+        fctx.ctx, fctx.co, fctx.x = ctx, co, [t.clone() for t in x]
+        fctx.args = (max_iters, check_every, adj_tol)
+        fctx.info = {"iterations": done, "residual": res}
+        return tuple(x)
+
+    @staticmethod
+    def backward(fctx, *grads):
+        ctx, co = fctx.ctx, fctx.co
+        max_iters, check_every, adj_tol = fctx.args
+        T.thiim_set_coeffs(ctx, co)
+        lam = [(g if g is not None else torch.zeros_like(co[0])).clone().contiguous() for g in grads]
+        gco = [torch.zeros_like(co[0]) for _ in range(28)]
+        T.thiim_adjoint_steady(ctx, lam, gco, fctx.x, max_iters, check_every, adj_tol)
+        return (None, None, None, None, None, *gco)
+
+
 class Differentiable:
     """A THIIM_C128 context with differentiable coefficient building and solving."""
 
@@ -79,6 +111,13 @@ class Differentiable:
         if every > 64:
             raise ValueError("checkpoint interval above the library's segment limit (64)")
         return _Solve.apply(self.ctx, int(n_iters), int(every), *coeffs)
+
+    def solve_steady(self, coeffs, tol=1e-10, max_iters=1000000, check_every=500, adjoint_tol=None):
+        """Iterate from zero until the residual is <= tol (or max_iters); the backward
+        pass is the steady-state adjoint (thiim_adjoint_steady), i.e. the gradient of
+        the fixed point, valid once the forward solve has converged."""
+        return _SolveSteady.apply(self.ctx, float(tol), int(max_iters), int(check_every),
+                                  float(tol if adjoint_tol is None else adjoint_tol), *coeffs)
 
     def close(self):
         if self.ctx:

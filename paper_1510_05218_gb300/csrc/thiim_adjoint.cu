@@ -18,6 +18,13 @@
 // Kernel R1 computes lh (kept in scratch), lam_H and the H gradients; kernel
 // R2 the new lam_E and the E gradients.  Both are gather kernels, one thread
 // per cell (the adjoint is not the benchmarked path), in FP64.
+//
+// Steady state (thiim_adjoint_steady): at a fixed point x* = F(x*) every
+// state of the reverse iteration is x*, so its gradient contributions sum to
+// (dF/da)^H lam* with lam* = sum_k (M^H)^k g, the solution of the adjoint
+// fixed point lam* = M^H lam* + g.  The contributions are linear in lam, so
+// the iteration propagates lam alone (GRAD = false) while adding every new
+// term into lam*, and the gradient kernels run once, on lam*.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <string.h>
@@ -40,11 +47,12 @@ __constant__ Rule c_rules[12] = {
 
 struct AdjArgs {
     double2 *lam[12];        // in: adjoint of x^{n+1}; out: adjoint of x^n
-    double2 *grad[28];       // accumulated
-    const double2 *xn[12];   // x^n
-    const double2 *xn1[12];  // x^{n+1}
+    double2 *grad[28];       // accumulated (GRAD kernels only)
+    const double2 *xn[12];   // x^n (GRAD kernels only)
+    const double2 *xn1[12];  // x^{n+1} (GRAD kernels only)
     const double2 *co[28];
     double2 *lh[6];          // scratch: adjoint of H^{n+1/2}
+    double2 *acc[12];        // if acc[0]: acc += the new lam (steady-state sum)
     int nx, ny, nz;
     unsigned bc;
 };
@@ -69,6 +77,8 @@ __device__ __forceinline__ long long shifted(int i, int j, int k, int d, int off
     return ((long long)q[2] * a.ny + q[1]) * a.nx + q[0];
 }
 
+// GRAD = false: propagate lam only (no coefficient gradients, x not read).
+template <bool GRAD>
 __global__ void adjoint_h_kernel(const AdjArgs a) {
     const size_t n = (size_t)a.nx * a.ny * a.nz;
     for (size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (size_t)gridDim.x * blockDim.x) {
@@ -86,23 +96,28 @@ __global__ void adjoint_h_kernel(const AdjArgs a) {
         for (int h = 0; h < 6; ++h) {
             const Rule r = c_rules[h];
             const double2 lh = cadd(a.lam[h][p], A[h / 2]);
-            // D^- of the full E component this split reads, from x^n
-            const long long q = shifted(i, j, k, r.d, -1, a);
-            const double2 f0 = cadd(a.xn[r.a][p], a.xn[r.b][p]);
-            const double2 f1 = q < 0 ? c2(0, 0) : cadd(a.xn[r.a][q], a.xn[r.b][q]);
-            const double2 dm = cscale((double)r.sign, csub(f0, f1));
-            // g += lh * conj(v)  ==  conj(conj(lh) * v)
-            const double2 gt = conjmul(a.xn[h][p], lh);
-            const double2 gc = conjmul(dm, lh);
-            a.grad[T0 + h][p] = cadd(a.grad[T0 + h][p], gt);
-            a.grad[C0 + h][p] = cadd(a.grad[C0 + h][p], gc);
-            if (r.src >= 0) a.grad[r.src][p] = cadd(a.grad[r.src][p], lh);
+            if (GRAD) {
+                // D^- of the full E component this split reads, from x^n
+                const long long q = shifted(i, j, k, r.d, -1, a);
+                const double2 f0 = cadd(a.xn[r.a][p], a.xn[r.b][p]);
+                const double2 f1 = q < 0 ? c2(0, 0) : cadd(a.xn[r.a][q], a.xn[r.b][q]);
+                const double2 dm = cscale((double)r.sign, csub(f0, f1));
+                // g += lh * conj(v)  ==  conj(conj(lh) * v)
+                const double2 gt = conjmul(a.xn[h][p], lh);
+                const double2 gc = conjmul(dm, lh);
+                a.grad[T0 + h][p] = cadd(a.grad[T0 + h][p], gt);
+                a.grad[C0 + h][p] = cadd(a.grad[C0 + h][p], gc);
+                if (r.src >= 0) a.grad[r.src][p] = cadd(a.grad[r.src][p], lh);
+            }
             a.lh[h][p] = lh;
-            a.lam[h][p] = conjmul(a.co[T0 + h][p], lh);
+            const double2 nl = conjmul(a.co[T0 + h][p], lh);
+            a.lam[h][p] = nl;
+            if (a.acc[0]) a.acc[h][p] = cadd(a.acc[h][p], nl);
         }
     }
 }
 
+template <bool GRAD>
 __global__ void adjoint_e_kernel(const AdjArgs a) {
     const size_t n = (size_t)a.nx * a.ny * a.nz;
     for (size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (size_t)gridDim.x * blockDim.x) {
@@ -120,14 +135,18 @@ __global__ void adjoint_e_kernel(const AdjArgs a) {
         for (int e = 6; e < 12; ++e) {
             const Rule r = c_rules[e];
             const double2 mu = a.lam[e][p];
-            const long long q = shifted(i, j, k, r.d, +1, a);
-            const double2 f0 = cadd(a.xn1[r.a][p], a.xn1[r.b][p]);
-            const double2 f1 = q < 0 ? c2(0, 0) : cadd(a.xn1[r.a][q], a.xn1[r.b][q]);
-            const double2 dp = cscale((double)r.sign, csub(f1, f0));
-            a.grad[T0 + e][p] = cadd(a.grad[T0 + e][p], conjmul(a.xn[e][p], mu));
-            a.grad[C0 + e][p] = cadd(a.grad[C0 + e][p], conjmul(dp, mu));
-            if (r.src >= 0) a.grad[r.src][p] = cadd(a.grad[r.src][p], mu);
-            a.lam[e][p] = cadd(conjmul(a.co[T0 + e][p], mu), B[(e - 6) / 2]);
+            if (GRAD) {
+                const long long q = shifted(i, j, k, r.d, +1, a);
+                const double2 f0 = cadd(a.xn1[r.a][p], a.xn1[r.b][p]);
+                const double2 f1 = q < 0 ? c2(0, 0) : cadd(a.xn1[r.a][q], a.xn1[r.b][q]);
+                const double2 dp = cscale((double)r.sign, csub(f1, f0));
+                a.grad[T0 + e][p] = cadd(a.grad[T0 + e][p], conjmul(a.xn[e][p], mu));
+                a.grad[C0 + e][p] = cadd(a.grad[C0 + e][p], conjmul(dp, mu));
+                if (r.src >= 0) a.grad[r.src][p] = cadd(a.grad[r.src][p], mu);
+            }
+            const double2 nl = cadd(conjmul(a.co[T0 + e][p], mu), B[(e - 6) / 2]);
+            a.lam[e][p] = nl;
+            if (a.acc[0]) a.acc[e][p] = cadd(a.acc[e][p], nl);
         }
     }
 }
@@ -255,10 +274,139 @@ extern "C" int thiim_adjoint_iterate(thiim_ctx *c, void *const lambda[THIIM_N_FI
             a.xn[i] = (const double2 *)(m == 0 ? fwd_checkpoint[i] : c->adj_states[m - 1][i]);
             a.xn1[i] = (const double2 *)c->adj_states[m][i];
         }
-        adjoint_h_kernel<<<(unsigned)blocks, 256, 0, c->stream>>>(a);
-        adjoint_e_kernel<<<(unsigned)blocks, 256, 0, c->stream>>>(a);
+        adjoint_h_kernel<true><<<(unsigned)blocks, 256, 0, c->stream>>>(a);
+        adjoint_e_kernel<true><<<(unsigned)blocks, 256, 0, c->stream>>>(a);
         if (cudaGetLastError() != cudaSuccess) return THIIM_ERR_CUDA;
     }
+    return THIIM_OK;
+}
+
+namespace {
+
+struct NormArgs {
+    const double2 *w[12];
+    const double2 *s[12];
+    size_t n;
+    double *partials;
+};
+
+// Per-CTA |w|^2 and |s|^2 over the 12 arrays (fixed-order reductions).
+__global__ void __launch_bounds__(256) adj_norm_kernel(const NormArgs a) {
+    __shared__ double rw[8], rs[8];
+    double aw = 0.0, as = 0.0;
+    for (size_t p = (size_t)blockIdx.x * 256 + threadIdx.x; p < a.n; p += (size_t)gridDim.x * 256) {
+        for (int i = 0; i < 12; ++i) {
+            const double2 u = a.w[i][p], v = a.s[i][p];
+            aw += u.x * u.x + u.y * u.y;
+            as += v.x * v.x + v.y * v.y;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        aw += __shfl_down_sync(0xffffffffu, aw, o);
+        as += __shfl_down_sync(0xffffffffu, as, o);
+    }
+    if ((threadIdx.x & 31) == 0) { rw[threadIdx.x >> 5] = aw; rs[threadIdx.x >> 5] = as; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tw = 0.0, ts = 0.0;
+        for (int i = 0; i < 8; ++i) { tw += rw[i]; ts += rs[i]; }
+        a.partials[2 * blockIdx.x] = tw;
+        a.partials[2 * blockIdx.x + 1] = ts;
+    }
+}
+
+// |last term| / |sum| on the host (synchronises the stream).
+int adj_rel(thiim_ctx *c, void *const *w, void *const *s, double *rel) {
+    const size_t ctas = 4 * (size_t)c->num_sms;
+    int st = ensure_partials(c, ctas);
+    if (st) return st;
+    if (!c->adj_norms && cudaMalloc(&c->adj_norms, 2 * sizeof(double)) != cudaSuccess) return THIIM_ERR_NOMEM;
+    NormArgs a;
+    for (int i = 0; i < 12; ++i) { a.w[i] = (const double2 *)w[i]; a.s[i] = (const double2 *)s[i]; }
+    a.n = c->n_cells;
+    a.partials = c->partials;
+    adj_norm_kernel<<<(unsigned)ctas, 256, 0, c->stream>>>(a);
+    if (cudaGetLastError() != cudaSuccess) return THIIM_ERR_CUDA;
+    if (finalize_norms(c->partials, ctas, c->adj_norms, c->stream) != cudaSuccess) return THIIM_ERR_CUDA;
+    double h[2];
+    if (cudaMemcpyAsync(h, c->adj_norms, sizeof(h), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess)
+        return THIIM_ERR_CUDA;
+    if (!isfinite(h[0]) || !isfinite(h[1])) return THIIM_ERR_NONFINITE;
+    *rel = h[1] > 0.0 ? sqrt(h[0] / h[1]) : 0.0;
+    return THIIM_OK;
+}
+
+}  // namespace
+
+extern "C" int thiim_adjoint_steady(thiim_ctx *c, void *const lambda[THIIM_N_FIELDS],
+                                    void *const grad_coeff[THIIM_N_COEFFS],
+                                    const void *const x_star[THIIM_N_FIELDS], int max_iters, int check_every,
+                                    double tol, int *iters_out, double *rel_out) {
+    if (!c || !lambda || !grad_coeff || !x_star || max_iters < 1 || check_every < 1 || !(tol >= 0.0) ||
+        !isfinite(tol))
+        return THIIM_ERR_ARG;
+    if (c->precision != THIIM_C128) return THIIM_ERR_ARG;
+    if (!c->have_coeffs || c->use_table) return THIIM_ERR_STATE;
+    for (int i = 0; i < THIIM_N_FIELDS; ++i)
+        if (!lambda[i] || !x_star[i] || !aligned(lambda[i], 16) || !aligned(x_star[i], 16))
+            return lambda[i] && x_star[i] ? THIIM_ERR_ALIGN : THIIM_ERR_ARG;
+    for (int i = 0; i < THIIM_N_COEFFS; ++i)
+        if (!grad_coeff[i] || !aligned(grad_coeff[i], 16)) return grad_coeff[i] ? THIIM_ERR_ALIGN : THIIM_ERR_ARG;
+    int st = ensure_adjoint_scratch(c, 1);
+    if (st) return st;
+    void **w = c->adj_states[0];     // the current term (M^H)^k g
+    const size_t bytes = c->n_cells * 16;
+    for (int i = 0; i < THIIM_N_FIELDS; ++i)
+        if (cudaMemcpyAsync(w[i], lambda[i], bytes, cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
+            return THIIM_ERR_CUDA;
+    AdjArgs a;
+    memset(&a, 0, sizeof(a));
+    for (int i = 0; i < THIIM_N_FIELDS; ++i) {
+        a.lam[i] = (double2 *)w[i];
+        a.acc[i] = (double2 *)lambda[i];          // lam* so far (starts as g)
+    }
+    for (int i = 0; i < THIIM_N_COEFFS; ++i) a.co[i] = (const double2 *)c->coeff[i];
+    for (int i = 0; i < 6; ++i) a.lh[i] = (double2 *)c->adj_lh[i];
+    a.nx = c->nx; a.ny = c->ny; a.nz = c->nz;
+    a.bc = c->bc;
+    size_t blocks = (c->n_cells + 255) / 256;
+    if (blocks > 8u * (size_t)c->num_sms) blocks = 8u * (size_t)c->num_sms;
+    int k = 1;
+    double rel = 1.0;
+    bool have_rel = false;
+    while (k < max_iters) {
+        adjoint_h_kernel<false><<<(unsigned)blocks, 256, 0, c->stream>>>(a);
+        adjoint_e_kernel<false><<<(unsigned)blocks, 256, 0, c->stream>>>(a);
+        if (cudaGetLastError() != cudaSuccess) return THIIM_ERR_CUDA;
+        ++k;
+        have_rel = false;
+        if (tol > 0.0 && (k % check_every == 0)) {
+            st = adj_rel(c, w, lambda, &rel);
+            if (st) return st;
+            have_rel = true;
+            if (rel <= tol) break;
+        }
+    }
+    if (!have_rel) {
+        st = adj_rel(c, w, lambda, &rel);
+        if (st) return st;
+    }
+    // Gradient of lam*: the gradient kernels on a copy (they overwrite their lam).
+    for (int i = 0; i < THIIM_N_FIELDS; ++i)
+        if (cudaMemcpyAsync(w[i], lambda[i], bytes, cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
+            return THIIM_ERR_CUDA;
+    for (int i = 0; i < THIIM_N_FIELDS; ++i) {
+        a.acc[i] = nullptr;
+        a.xn[i] = (const double2 *)x_star[i];
+        a.xn1[i] = (const double2 *)x_star[i];
+    }
+    for (int i = 0; i < THIIM_N_COEFFS; ++i) a.grad[i] = (double2 *)grad_coeff[i];
+    adjoint_h_kernel<true><<<(unsigned)blocks, 256, 0, c->stream>>>(a);
+    adjoint_e_kernel<true><<<(unsigned)blocks, 256, 0, c->stream>>>(a);
+    if (cudaGetLastError() != cudaSuccess) return THIIM_ERR_CUDA;
+    if (iters_out) *iters_out = k;
+    if (rel_out) *rel_out = rel;
     return THIIM_OK;
 }
 

@@ -545,6 +545,7 @@ void thiim_destroy(thiim_ctx *c) {
     if (c->partials) cudaFree(c->partials);
     if (c->norms) cudaFree(c->norms);
     if (c->power) cudaFree(c->power);
+    if (c->adj_norms) cudaFree(c->adj_norms);
     if (c->pml) cudaFree(c->pml);
     if (c->flag) cudaFree(c->flag);
     delete c;

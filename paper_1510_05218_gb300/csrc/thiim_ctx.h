@@ -46,6 +46,7 @@ struct thiim_ctx {
     void *adj_lh[6];             // adjoint of H^{n+1/2}
     void *adj_states[THIIM_MAX_ADJOINT_SEGMENT][THIIM_N_FIELDS];  // recomputed iterates
     int adj_cap;                 // complete recomputed-iterate sets allocated
+    double *adj_norms;           // device: 2 doubles, thiim_adjoint_steady's convergence check
 };
 
 

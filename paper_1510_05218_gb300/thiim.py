@@ -74,6 +74,9 @@ def load_library(build_if_missing: bool = False):
     lib.thiim_batch_iterate.restype = ctypes.c_int
     lib.thiim_adjoint_iterate.argtypes = [vp, P12, P28, P12, ctypes.c_int]
     lib.thiim_adjoint_iterate.restype = ctypes.c_int
+    lib.thiim_adjoint_steady.argtypes = [vp, P12, P28, P12, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                         ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
+    lib.thiim_adjoint_steady.restype = ctypes.c_int
     lib.thiim_build_coeffs_grad.argtypes = [vp, vp, vp, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                             ctypes.c_double, ctypes.c_double, P28, vp]
     lib.thiim_build_coeffs_grad.restype = ctypes.c_int
@@ -256,6 +259,17 @@ def thiim_adjoint_iterate(ctx, lam, grad_coeffs, checkpoint, n_back):
     _check("thiim_adjoint_iterate", load_library().thiim_adjoint_iterate(
         ctx, _ptrs(lam, 12, "lambda"), _ptrs(grad_coeffs, 28, "gradient"), _ptrs(checkpoint, 12, "field"),
         int(n_back)))
+
+
+def thiim_adjoint_steady(ctx, lam, grad_coeffs, x_star, max_iters, check_every=50, tol=0.0):
+    """Steady-state adjoint at the fixed point x_star: lam (in: g, out: lam*), gradient added to
+    grad_coeffs; returns (terms summed, |last term| / |lam*|)."""
+    k = ctypes.c_int()
+    r = ctypes.c_double()
+    _check("thiim_adjoint_steady", load_library().thiim_adjoint_steady(
+        ctx, _ptrs(lam, 12, "lambda"), _ptrs(grad_coeffs, 28, "gradient"), _ptrs(x_star, 12, "field"),
+        int(max_iters), int(check_every), float(tol), ctypes.byref(k), ctypes.byref(r)))
+    return k.value, r.value
 
 
 def thiim_build_coeffs_grad(ctx, eps_r, sigma_pml_e, omega, tau, k_s, amp, grad_coeffs, grad_eps_re):
