@@ -43,7 +43,7 @@ PRECISION_NOTE = {"c128": "with native FP64 arithmetic",
                   "pair": "with FP32-pair arithmetic (parity with the FP64 oracle <= 1e-12)",
                   "c64": "stored as complex64 with FP32 arithmetic"}
 FLOPS_PER_LUP = 248                                  # the paper's count (Sec. III-A)
-SWEEP_SRC = os.path.join(ROOT, "paper_1510_05218_gb300", "csrc", "thiim_sweep.cuh")
+SWEEP_SRC = [os.path.join(ROOT, "paper_1510_05218_gb300", "csrc", f) for f in ("thiim_sweep.cuh", "thiim_internal.h")]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "sweep_traffic.json")
 
 
@@ -64,8 +64,12 @@ def _peaks():
 
 
 def _sweep_sha():
-    with open(SWEEP_SRC, "rb") as fh:
-        return hashlib.sha256(fh.read()).hexdigest()[:16]
+    """Hash of the sweep's source and of its tile configuration."""
+    h = hashlib.sha256()
+    for path in SWEEP_SRC:
+        with open(path, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def _traffic(kernel_key, cells):

@@ -17,8 +17,11 @@ namespace thiim {
 
 bool aligned(const void *p, size_t a) { return ((uintptr_t)p % a) == 0; }
 
-int tiles_x(const thiim_ctx *c) { return (c->nx + SWEEP_TX - 1) / SWEEP_TX; }
-int tiles_y(const thiim_ctx *c) { return (c->ny + SWEEP_TY - 1) / SWEEP_TY; }
+// Tile shape by precision (matches Tile<A> of the kernels the precision runs).
+int tile_w(const thiim_ctx *c) { return c->precision == THIIM_C128_PAIR ? SWEEP_PAIR_TX : SWEEP_TX; }
+int tile_h(const thiim_ctx *c) { return c->precision == THIIM_C128_PAIR ? SWEEP_PAIR_TY : SWEEP_TY; }
+int tiles_x(const thiim_ctx *c) { return (c->nx + tile_w(c) - 1) / tile_w(c); }
+int tiles_y(const thiim_ctx *c) { return (c->ny + tile_h(c) - 1) / tile_h(c); }
 
 // Planes per CTA: enough CTAs along z that the grid covers every SM several
 // times, but at least 8 planes so the one-plane prologue and lookahead of a

@@ -36,6 +36,34 @@ template <typename V>
 __device__ __forceinline__ V ldg_as(const void *base, size_t i) {
     return __ldg(reinterpret_cast<const V *>(base) + i);
 }
+// L2 eviction priority of a load: createpolicy gives a cache policy that
+// ld.global.L2::cache_hint applies to the lines it brings in.
+__device__ __forceinline__ uint64_t l2_evict_last() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+template <typename V> __device__ __forceinline__ V ldg_hint(const void *base, size_t i, uint64_t pol);
+template <> __device__ __forceinline__ double2 ldg_hint<double2>(const void *base, size_t i, uint64_t pol) {
+    double2 v;
+    asm volatile("ld.global.nc.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;"
+                 : "=d"(v.x), "=d"(v.y) : "l"(reinterpret_cast<const double2 *>(base) + i), "l"(pol));
+    return v;
+}
+template <> __device__ __forceinline__ float2 ldg_hint<float2>(const void *base, size_t i, uint64_t pol) {
+    float2 v;
+    asm volatile("ld.global.nc.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;"
+                 : "=f"(v.x), "=f"(v.y) : "l"(reinterpret_cast<const float2 *>(base) + i), "l"(pol));
+    return v;
+}
+template <> __device__ __forceinline__ float4 ldg_hint<float4>(const void *base, size_t i, uint64_t pol) {
+    float4 v;
+    asm volatile("ld.global.nc.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "l"(reinterpret_cast<const float4 *>(base) + i), "l"(pol));
+    return v;
+}
+
 template <typename V>
 __device__ __forceinline__ void stg_as(void *base, size_t i, V v) {
     reinterpret_cast<V *>(base)[i] = v;
@@ -50,6 +78,9 @@ struct Native {
     static constexpr int min_blocks = sizeof(R) == 8 ? 3 : 5;
     __device__ static __forceinline__ Z zero() { Z z; z.x = R(0); z.y = R(0); return z; }
     __device__ static __forceinline__ Z ld_field(const void *b, size_t i) { return ldg_as<Z>(b, i); }
+    __device__ static __forceinline__ Z ld_field_hint(const void *b, size_t i, uint64_t pol) {
+        return ldg_hint<Z>(b, i, pol);
+    }
     __device__ static __forceinline__ Z ld_coef(const void *b, size_t i) { return ldg_as<Z>(b, i); }
     __device__ static __forceinline__ void st_field(void *b, size_t i, Z v) { stg_as<Z>(b, i, v); }
     __device__ static __forceinline__ Z add(Z a, Z b) { Z r; r.x = a.x + b.x; r.y = a.y + b.y; return r; }
@@ -146,6 +177,12 @@ struct PairArith {
     __device__ static __forceinline__ Z ld_field(const void *b, size_t i) {
         if (IN_PAIRS) return from_f4(ldg_as<float4>(b, i));
         const double2 v = ldg_as<double2>(b, i);
+        Z z; z.x = split_double(v.x); z.y = split_double(v.y);
+        return z;
+    }
+    __device__ static __forceinline__ Z ld_field_hint(const void *b, size_t i, uint64_t pol) {
+        if (IN_PAIRS) return from_f4(ldg_hint<float4>(b, i, pol));
+        const double2 v = ldg_hint<double2>(b, i, pol);
         Z z; z.x = split_double(v.x); z.y = split_double(v.y);
         return z;
     }

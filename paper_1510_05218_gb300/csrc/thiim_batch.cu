@@ -63,7 +63,7 @@ batch_kernel(const BatchList L, int parity, int want_norm) {
             sa.partials = nullptr;
         }
         __syncthreads();
-        sweep_tile<A, SWEEP_TX, SWEEP_TY, SWEEP_NT, MODE>(sa, it.y % d.tiles, it.y / d.tiles,
+        sweep_tile<A, Tile<A>::TX, Tile<A>::TY, SWEEP_NT, MODE>(sa, it.y % d.tiles, it.y / d.tiles,
                                                           want_norm ? L.partials + 2 * (size_t)item : nullptr);
         __syncthreads();   // sa and the tile's shared arrays are reused by the next item
     }

@@ -8,7 +8,8 @@
 
 namespace thiim {
 
-// Sweep tile: TX x TY cells per CTA, NT threads, MINB resident CTAs per SM
+// Sweep tile: TX x TY cells per CTA (TX fixed at 32 in the shipped build; the
+// macros let a build try other shapes), NT threads, MINB resident CTAs per SM
 // requested from the register allocator (0 = no request).
 #ifndef THIIM_SWEEP_TY
 #define THIIM_SWEEP_TY 8
@@ -19,10 +20,31 @@ namespace thiim {
 #ifndef THIIM_SWEEP_MINB
 #define THIIM_SWEEP_MINB 0
 #endif
-constexpr int SWEEP_TX = 32;
+#ifndef THIIM_SWEEP_TX
+#define THIIM_SWEEP_TX 32
+#endif
+#ifndef THIIM_SWEEP_PAIR_TX
+#define THIIM_SWEEP_PAIR_TX 64
+#endif
+#ifndef THIIM_SWEEP_PAIR_TY
+#define THIIM_SWEEP_PAIR_TY 4
+#endif
+constexpr int SWEEP_TX = THIIM_SWEEP_TX;
 constexpr int SWEEP_TY = THIIM_SWEEP_TY;
 constexpr int SWEEP_NT = THIIM_SWEEP_NT;
 constexpr int SWEEP_MINB = THIIM_SWEEP_MINB;
+constexpr int SWEEP_PAIR_TX = THIIM_SWEEP_PAIR_TX;
+constexpr int SWEEP_PAIR_TY = THIIM_SWEEP_PAIR_TY;
+
+// Tile of each arithmetic policy.  The FP32-pair sweeps use 64 x 4: their
+// 1 KB rows per array and CTA measured 3.5 % faster at 512^3 than 32 x 8
+// (complex64 and FP64 were fastest at 32 x 8).  Host code picks the same
+// shape by precision (tiles_x / tiles_y).
+template <typename A>
+struct Tile { static constexpr int TX = SWEEP_TX, TY = SWEEP_TY; };
+template <int I, int O>
+struct Tile<PairArith<I, O>> { static constexpr int TX = SWEEP_PAIR_TX, TY = SWEEP_PAIR_TY; };
+static_assert(SWEEP_PAIR_TX * SWEEP_PAIR_TY <= 2 * SWEEP_NT, "pair tile too large for the CTA");
 
 // Enqueue one fused iteration; grid = (tiles_x * tiles_y, chunks).
 cudaError_t launch_sweep_f64(const SweepArgs &a, dim3 grid, cudaStream_t s);

@@ -6,9 +6,9 @@ namespace thiim {
 
 cudaError_t launch_sweep_pair_in_c128(const SweepArgs &a, dim3 grid, cudaStream_t s, bool out_pairs) {
     if (out_pairs)
-        sweep_kernel<PairArith<0, 1>, SWEEP_TX, SWEEP_TY, SWEEP_NT, SWEEP_MINB><<<grid, SWEEP_NT, 0, s>>>(a);
+        sweep_kernel<PairArith<0, 1>, SWEEP_PAIR_TX, SWEEP_PAIR_TY, SWEEP_NT, SWEEP_MINB><<<grid, SWEEP_NT, 0, s>>>(a);
     else
-        sweep_kernel<PairArith<0, 0>, SWEEP_TX, SWEEP_TY, SWEEP_NT, SWEEP_MINB><<<grid, SWEEP_NT, 0, s>>>(a);
+        sweep_kernel<PairArith<0, 0>, SWEEP_PAIR_TX, SWEEP_PAIR_TY, SWEEP_NT, SWEEP_MINB><<<grid, SWEEP_NT, 0, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -18,16 +18,16 @@ cudaError_t launch_sweep_f32_tbl(const SweepArgs &a, dim3 grid, cudaStream_t s) 
 
 cudaError_t launch_sweep_pair_tbl(const SweepArgs &a, dim3 grid, cudaStream_t s, bool in_pairs, bool out_pairs) {
     if (!in_pairs && out_pairs)
-        sweep_kernel<PairArith<0, 1>, SWEEP_TX, SWEEP_TY, SWEEP_NT, SWEEP_MINB, SWEEP_PLAIN, true>
+        sweep_kernel<PairArith<0, 1>, SWEEP_PAIR_TX, SWEEP_PAIR_TY, SWEEP_NT, SWEEP_MINB, SWEEP_PLAIN, true>
             <<<grid, SWEEP_NT, 0, s>>>(a);
     else if (!in_pairs)
-        sweep_kernel<PairArith<0, 0>, SWEEP_TX, SWEEP_TY, SWEEP_NT, SWEEP_MINB, SWEEP_PLAIN, true>
+        sweep_kernel<PairArith<0, 0>, SWEEP_PAIR_TX, SWEEP_PAIR_TY, SWEEP_NT, SWEEP_MINB, SWEEP_PLAIN, true>
             <<<grid, SWEEP_NT, 0, s>>>(a);
     else if (out_pairs)
-        sweep_kernel<PairArith<1, 1>, SWEEP_TX, SWEEP_TY, SWEEP_NT, SWEEP_MINB, SWEEP_PLAIN, true>
+        sweep_kernel<PairArith<1, 1>, SWEEP_PAIR_TX, SWEEP_PAIR_TY, SWEEP_NT, SWEEP_MINB, SWEEP_PLAIN, true>
             <<<grid, SWEEP_NT, 0, s>>>(a);
     else
-        sweep_kernel<PairArith<1, 0>, SWEEP_TX, SWEEP_TY, SWEEP_NT, SWEEP_MINB, SWEEP_PLAIN, true>
+        sweep_kernel<PairArith<1, 0>, SWEEP_PAIR_TX, SWEEP_PAIR_TY, SWEEP_NT, SWEEP_MINB, SWEEP_PLAIN, true>
             <<<grid, SWEEP_NT, 0, s>>>(a);
     return cudaGetLastError();
 }

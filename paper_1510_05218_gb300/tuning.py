@@ -11,7 +11,8 @@ for the GPU kernels here:
 * ``gpu_footprint`` gives, for a launch configuration (iterations per launch,
   z planes per CTA), the shared memory one CTA needs and the data a launch
   must find again in L2; ``gpu_code_balance`` the DRAM bytes per cell and
-  iteration including the halo the 32 x 8 tiles re-read.  A candidate is
+  iteration including the halo the tiles re-read (32 x 8 cells; 64 x 4 for
+  the FP32-pair sweeps).  A candidate is
   admitted if its shared memory fits a CTA, its L2 set stays within half of
   L2 (the paper's "half the cache is usable for tile data" rule, Sec. III-C)
   and its grid fills the resident slots; the library default is always a
@@ -55,13 +56,19 @@ def code_balance_diamond(d_w: int) -> float:
 
 # ---- the same reasoning for the GPU kernels -----------------------------------------
 
-TX, TY = 32, 8                        # cells of one CTA's column
+TX, TY = 32, 8                        # cells of one CTA's column (complex128, complex64)
+PAIR_TX, PAIR_TY = 64, 4              # the FP32-pair sweeps' column
 SMEM_PER_SM = 228 * 1024              # bytes of shared memory per SM (GB300)
 SMEM_PER_CTA = 227 * 1024
 
 
 def elem_bytes(precision: int) -> int:
     return 8 if precision == 1 else 16
+
+
+def tile(precision: int):
+    """(TX, TY) of the sweep kernels a precision runs."""
+    return (PAIR_TX, PAIR_TY) if precision == 2 else (TX, TY)
 
 
 def gpu_footprint(precision: int, temporal: int, zchunk: int, ctas: int, n_sm: int, l2_bytes: int):
@@ -80,6 +87,7 @@ def gpu_footprint(precision: int, temporal: int, zchunk: int, ctas: int, n_sm: i
     Sec. III-C) and the grid has at least one CTA per resident slot.
     """
     b = elem_bytes(precision)
+    TX, TY = tile(precision)
     if temporal == 1:
         smem = b * 3 * 2 * ((TX + 2) * (TY + 2) + (TX + 1) * (TY + 1))
         per_sm = 5 if precision == 1 else (3 if precision == 0 else 2)
@@ -105,6 +113,7 @@ def gpu_code_balance(precision: int, temporal: int, zchunk: int) -> float:
     read x^0 on the grown regions once and write x^2 once, per two iterations.
     """
     b = elem_bytes(precision)
+    TX, TY = tile(precision)
     cells = TX * TY
     z = max(1, zchunk)
     if temporal == 1:
@@ -140,7 +149,8 @@ def autotune(ctx, fields, nx, ny, nz, precision, iters=20, repeats=2, stream=Non
     from . import thiim as T
 
     props = torch.cuda.get_device_properties(fields[0].device)
-    tiles = math.ceil(nx / TX) * math.ceil(ny / TY)
+    tx, ty = tile(precision)
+    tiles = math.ceil(nx / tx) * math.ceil(ny / ty)
     cands = candidates(precision, nz, tiles, props.multi_processor_count, props.L2_cache_size)
     saved = [f.clone() for f in fields]
     times = {}

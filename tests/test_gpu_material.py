@@ -37,7 +37,7 @@ def _lib():
 
 
 def _stack(name):
-    if name == "ragged":   # 40 x 20: x tiles 32 + 8, y tiles 8 + 8 + 4
+    if name == "ragged":   # 40 x 20: 32 x 8 tiles 32 + 8 by 8 + 8 + 4; 64 x 4 tiles (pair) 40 by 5 x 4
         return LayeredStack(nx=40, ny=20, nz=48, seed=3)
     return stack_config(name)
 
