@@ -209,9 +209,11 @@ int thiim_build_coeffs_jones(thiim_ctx *ctx, const void *eps_r,
 /*
  * thiim_absorbed_power — P = 1/2 sum over cells of sigma |E|^2 for the
  * context's current fields (E = the full components, split sums), summed in
- * FP64 in a fixed order (deterministic).  Divided by the incident power of
- * the plane wave it is the absorption of a solar cell at one wavelength and
- * polarisation, the quantity of the paper's spectrum runs (Sec. V).
+ * FP64 in a fixed order (deterministic).  At the fixed point the power
+ * dissipated in those cells is cos(omega tau / 2) P (the loss term of Eqs. 3
+ * and 5 carries the phase e^{+-i omega tau/2}); over the incident power of
+ * the plane wave that is the absorption of a solar cell at one wavelength
+ * and polarisation, the quantity of the paper's spectrum runs (Sec. V).
  *   sigma: device array of nx*ny*nz conductivities (layout as the fields),
  *          e.g. omega Im(eps_r) on the absorbing layer and 0 elsewhere.
  *   power: host double receiving P.

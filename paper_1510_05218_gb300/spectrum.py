@@ -6,8 +6,15 @@ spectrum for one solar-cell configuration takes 80-160 simulations (Sec. V).
 Here each (wavelength, polarisation) pair is a solve with its own context;
 their coefficients are built on the GPU (thiim_build_coeffs_jones), they
 iterate together in thiim_batch_iterate, and each reports its absorbed power
-(thiim_absorbed_power).  The absorption is that power over the incident one,
-and the unpolarised absorption is the mean over the x- and y-polarised runs.
+(thiim_absorbed_power).  The absorption is the power dissipated in the
+absorber over the incident power, and the unpolarised absorption is the mean
+over the x- and y-polarised runs.
+
+Dissipated power: at the fixed point the loss term of Eqs. 3 and 5 carries the
+phase e^{+-i omega tau / 2}, so the discrete Poynting balance of a slab reads
+Re(flux in - flux out) = cos(omega tau / 2) sum sigma |E|^2 (an identity of
+the discrete equations); the power dissipated is cos(omega tau / 2) times
+P = 1/2 sum sigma |E|^2.
 
 Incident power: the discrete plane wave E_x(k) = A e^{-i kappa k},
 H_y = -dE_x/(i omega_t) (2 sin(kappa/2) = omega_t = 2 sin(omega tau/2)/tau)
@@ -76,7 +83,8 @@ def absorption_spectrum(eps, lambdas, sigma_pml_e, sigma_pml_h, k_s, tau, absorb
         for s in solves:
             p_abs = T.thiim_absorbed_power(s["ctx"], s["sigma"])
             out["power"].append(p_abs)
-            out["A"][s["pol"]].append(p_abs / incident_power(s["omega"], tau, nx, ny))
+            dissipated = math.cos(s["omega"] * tau / 2.0) * p_abs
+            out["A"][s["pol"]].append(dissipated / incident_power(s["omega"], tau, nx, ny))
         out["A_unpolarised"] = [sum(out["A"][p][i] for p in polarisations) / len(polarisations)
                                 for i in range(len(lambdas))]
         return out
