@@ -168,6 +168,19 @@ def cpu_oracle_rate(stack, planes, target_s, threads):
     return cells * done / el / 1e6, dict(planes=[k0, k1], cells=cells, iters=done, seconds=el)
 
 
+def _cpu_model():
+    """The host CPU as lscpu names it (for the CPU-baseline record)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.machine()
+
+
 def run_reference(args):
     rank, world, _ = _dist()
     if rank != 0:
@@ -192,7 +205,8 @@ def run_reference(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": "%s: %dx%dx%d textured thin-film stack, complex128" % (args.workload, st.nx, st.ny, st.nz),
                    "parallelism": "host cores"},
-        "cpu_baseline": {"value": value, "unit": "MLUP/s", "cores": threads, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "MLUP/s", "cores": threads, "kind": "oracle", "sample": sample,
+                         "cpu_model": _cpu_model()},
         "e2e": {"value": value, "unit": "MLUP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(out), flush=True)
@@ -560,7 +574,10 @@ def run_ours(args):
     if not args.no_cpu_baseline and world == 1:
         threads = os.cpu_count() or 1
         rate, info = cpu_oracle_rate(st, args.ref_planes, args.ref_seconds, threads)
-        cpu = {"value": rate, "unit": "MLUP/s", "cores": threads, "kind": "oracle",
+        rate1, info1 = cpu_oracle_rate(st, 2, 3.0, 1)
+        cpu = {"value": rate, "unit": "MLUP/s", "cores": threads, "kind": "oracle", "cpu_model": _cpu_model(),
+               "single_thread": {"value": rate1, "sample": "%d iterations of a %dx%dx2 slab in %.1f s"
+                                 % (info1["iters"], st.nx, st.ny, info1["seconds"])},
                "sample": "plain C FP64 oracle, OpenMP over z, on a %dx%dx%d slab (planes %d-%d) of the same "
                          "stack, %d iterations in %.1f s" % (st.nx, st.ny, args.ref_planes, info["planes"][0],
                                                              info["planes"][1], info["iters"], info["seconds"])}
