@@ -410,6 +410,39 @@ def _variant_spectrum(p, torch, precision, n_lambda, iters):
             "residual_max": max(r["residuals"])}
 
 
+def _variant_adjoint_steady(p, torch, stream, dev, terms, peak):
+    """Steady-state adjoint on the 128^3 stack: `terms` propagation steps of
+    thiim_adjoint_steady plus its one gradient evaluation (CUDA events)."""
+    from workloads import stack_config
+    st = stack_config("stack128")
+    ctx, co, fields, eps = _stack_problem(p, torch, st, "c128", stream, dev)
+    shape = (st.nz, st.ny, st.nx)
+    try:
+        lam = [torch.zeros(shape, dtype=torch.complex128, device=dev) for _ in range(6)] + \
+              [torch.full(shape, 1e-3, dtype=torch.complex128, device=dev) for _ in range(6)]
+        gco = [torch.zeros(shape, dtype=torch.complex128, device=dev) for _ in range(28)]
+        p.thiim_adjoint_steady(ctx, lam, gco, fields, 2, 2, 0.0)      # warm-up (scratch allocation)
+        torch.cuda.synchronize()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        p.thiim_adjoint_steady(ctx, lam, gco, fields, terms, terms, 0.0)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        ms = t0.elapsed_time(t1)
+    finally:
+        p.thiim_destroy(ctx)
+    del co, fields, eps, lam, gco
+    torch.cuda.empty_cache()
+    cells = st.nx * st.ny * st.nz
+    # per term and cell: lam, lh, the running sum and the t, c arrays read; lam, lh, the sum written
+    alg = (12 + 6 + 12 + 24) * 16 + (12 + 6 + 12) * 16
+    return {"value": cells * terms / (ms / 1e3) / 1e6, "unit": "MLUP/s (adjoint terms)", "dtype": "f64",
+            "terms": terms, "ms": ms, "alg_bytes_per_term": alg,
+            "frac_hbm": cells * terms * alg / (ms / 1e3) / 1e9 / peak,
+            "what": "thiim_adjoint_steady at 128^3: propagation kernels (FP64 gather, one thread per cell) "
+                    "and one gradient evaluation"}
+
+
 def run_grid_sweep(args):
     """MLUP/s against the cubic grid size (64^3 .. 512^3 in steps of 64), one
     JSON line per size and path — the GPU counterpart of the paper's grid-size
@@ -566,6 +599,7 @@ def run_ours(args):
         variants["mixed_c64_f64_defect"] = _variant_mixed(p, torch, st, stream, dev, 50, 4, 1)
         variants["batch32_" + args.precision] = _variant_batch(p, torch, args.precision, stream, dev, 200, 50, 1)
         variants["spectrum16x2_" + args.precision] = _variant_spectrum(p, torch, args.precision, 16, 200)
+        variants["adjoint_steady_128"] = _variant_adjoint_steady(p, torch, stream, dev, 200, peak)
 
     if rank != 0:
         return
