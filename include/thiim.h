@@ -385,7 +385,7 @@ int thiim_build_coeffs_grad(thiim_ctx *ctx, const void *eps_r, const double *sig
  *   ctx[0..nb-1]: contexts of one precision on one device, each with fields
  *                 and coefficients set; grids may differ in size.
  *   Every iteration of all still-active solves is ONE persistent launch that
- *   walks a list of (solve, 32x8 column, z chunk) items; check_every
+ *   walks a list of (solve, tile column, z chunk) items; check_every
  *   iterations (even, >= 2) and the per-solve residual run as one captured
  *   CUDA graph, after which solves whose residual (as thiim_residual) is
  *   <= tol, or which reached max_iters, leave the batch.

@@ -4,7 +4,7 @@
 // A spectrum sweep (the paper's application needs 80-160 runs per cell,
 // Sec. VI) is many small independent solves; launching each one separately
 // leaves most SMs idle on the small grids.  Here every active solve's work is
-// cut into items — one (32 x 8 column, z chunk) of one solve — and a grid of
+// cut into items — one (tile column, z chunk) of one solve — and a grid of
 // exactly as many CTAs as fit on the GPU walks the item list with a fixed
 // stride, so CTAs move from one solve to the next without a launch.  Items
 // read their solve's descriptor (field/coefficient pointers, sizes) into

@@ -46,7 +46,7 @@ def test_gpu_footprint_and_balance(precision, temporal):
     b = tuning.gpu_code_balance(precision, temporal, 64)
     alg = 52 * tuning.elem_bytes(precision)
     if temporal == 1:
-        assert alg < b < 1.3 * alg            # the halo re-read of 32x8 tiles: +10..30 %
+        assert alg < b < 1.3 * alg            # the halo re-read of the tiles: +10..30 %
     else:
         assert b < 0.75 * alg                 # two iterations per pass: fewer bytes per iteration
 
