@@ -35,8 +35,10 @@
  * Memory:  the caller owns every field, coefficient, lambda and gradient
  *          buffer (device memory); the library borrows the pointers until the
  *          next set call or thiim_destroy and owns only its context and
- *          scratch (a second field set of 12 arrays for the out-of-place
- *          sweep, and a few kilobytes of reduction partials).
+ *          scratch: a second field set of 12 arrays for the out-of-place
+ *          sweep, the FP32-pair copy of the coefficients (THIIM_C128_PAIR),
+ *          the work arrays of the adjoint and defect-correction calls when
+ *          those are used, and a few kilobytes of reduction partials.
  * Streams: all work is enqueued on the stream given to thiim_create (a
  *          cudaStream_t; NULL = legacy default stream) and returns before it
  *          runs, except calls documented as synchronising.
