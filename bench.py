@@ -355,6 +355,59 @@ def _variant_mixed(p, torch, st, stream, dev, inner, outer, warmup):
                     "FP64 defect sweep and a fold" % inner}
 
 
+def _variant_mixed_accuracy(p, torch, stream, dev):
+    """complex64 against FP64, the accuracy half of the metric: the 32^3 stack
+    solved to convergence by native FP64 (residual <= 1e-11) and by the mixed
+    solver (complex64 corrections, FP64 defect every 50, to its floor), both on
+    the GPU; the error is the relative L2 difference of each full component."""
+    from workloads import stack_config
+    st = stack_config("stack32")
+    shape = (st.nz, st.ny, st.nx)
+    eps = torch.from_numpy(st.eps()).to(dev)
+    args = (st.sigma_pml_e(), st.sigma_pml_h(), st.omega, st.tau, st.k_s, 1.0)
+    t0 = time.perf_counter()
+    ctx = p.thiim_create(st.nx, st.ny, st.nz, p.THIIM_C128, 3, stream)
+    try:
+        co64 = [torch.empty(shape, dtype=torch.complex128, device=dev) for _ in range(28)]
+        f64 = [torch.zeros(shape, dtype=torch.complex128, device=dev) for _ in range(12)]
+        with torch.cuda.stream(stream):
+            p.thiim_build_coeffs(ctx, eps, *args, co64)
+        p.thiim_set_tuning(ctx, 1, 4)
+        p.thiim_set_coeffs(ctx, co64)
+        p.thiim_set_fields(ctx, f64)
+        it64, r64 = 0, 1.0
+        while it64 < 400000 and r64 > 1e-11:
+            p.thiim_iterate(ctx, 2000)
+            it64 += 2000
+            r64 = p.thiim_residual(ctx)
+    finally:
+        p.thiim_destroy(ctx)
+    ctx = p.thiim_create(st.nx, st.ny, st.nz, p.THIIM_C64, 3, stream)
+    try:
+        co32 = [torch.empty(shape, dtype=torch.complex64, device=dev) for _ in range(28)]
+        work = [torch.zeros(shape, dtype=torch.complex64, device=dev) for _ in range(12)]
+        x64 = [torch.zeros(shape, dtype=torch.complex128, device=dev) for _ in range(12)]
+        with torch.cuda.stream(stream):
+            p.thiim_build_coeffs(ctx, eps, *args, co32)
+        p.thiim_set_tuning(ctx, 1, 4)
+        p.thiim_set_coeffs(ctx, co32)
+        p.thiim_set_fields(ctx, work)
+        outer, rm = p.thiim_mixed_solve(ctx, co64, x64, 50, 2000, 1e-7)
+    finally:
+        p.thiim_destroy(ctx)
+    torch.cuda.synchronize()
+    errs = []
+    for c in range(6):
+        ref = f64[2 * c] + f64[2 * c + 1]
+        mix = x64[2 * c] + x64[2 * c + 1]
+        errs.append(float(torch.linalg.vector_norm(mix - ref) / torch.linalg.vector_norm(ref)))
+    return {"max_rel_err_full_components": max(errs), "bound": 1e-6, "within_bound": max(errs) <= 1e-6,
+            "fp64_iterations": it64, "fp64_residual": r64, "mixed_outer_steps": outer, "mixed_fp64_residual": rm,
+            "seconds": time.perf_counter() - t0,
+            "what": "32^3 stack converged on the GPU by native FP64 and by thiim_mixed_solve (50 complex64 "
+                    "iterations per FP64 defect); relative L2 difference of the six full components"}
+
+
 def _variant_batch(p, torch, precision, stream, dev, iters, check, warmup):
     """The 32-solve spectrum sweep (uneven grids) in one persistent launch per iteration."""
     from workloads import batch_configs
@@ -597,6 +650,7 @@ def run_ours(args):
             variants[mode + "_material_table"] = _variant_sweep(p, torch, st, mode, stream, dev, iters, 1, 1, peak,
                                                                table=True)
         variants["mixed_c64_f64_defect"] = _variant_mixed(p, torch, st, stream, dev, 50, 4, 1)
+        variants["mixed_c64_f64_defect"]["accuracy_vs_fp64"] = _variant_mixed_accuracy(p, torch, stream, dev)
         variants["batch32_" + args.precision] = _variant_batch(p, torch, args.precision, stream, dev, 200, 50, 1)
         variants["spectrum16x2_" + args.precision] = _variant_spectrum(p, torch, args.precision, 16, 200)
         variants["adjoint_steady_128"] = _variant_adjoint_steady(p, torch, stream, dev, 200, peak)
