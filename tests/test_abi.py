@@ -2,8 +2,6 @@
 function that include/thiim.h declares (no compute calls are made here)."""
 import ctypes
 
-import pytest
-
 
 def test_header_declares_the_boundary_calls():
     import paper_1510_05218_gb300 as p
