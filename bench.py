@@ -356,9 +356,11 @@ def _variant_mixed(p, torch, st, stream, dev, inner, outer, warmup):
 
 def _variant_mixed_accuracy(p, torch, stream, dev):
     """complex64 against FP64, the accuracy half of the metric: the 32^3 stack
-    solved to convergence by native FP64 (residual <= 1e-11) and by the mixed
-    solver (complex64 corrections, FP64 defect every 50, to its floor), both on
-    the GPU; the error is the relative L2 difference of each full component."""
+    solved by native FP64 (to residual 1e-11 or 300k iterations; ~1e-10
+    reached) and by the mixed solver (complex64 corrections, FP64 defect every
+    50, run to its residual floor), both on the GPU; the error is the relative
+    L2 difference of each full component.  Stopping the mixed solve earlier,
+    at residual 1e-7, measured 3.2e-6: the slow tail of the iteration."""
     from workloads import stack_config
     st = stack_config("stack32")
     shape = (st.nz, st.ny, st.nx)
@@ -375,9 +377,9 @@ def _variant_mixed_accuracy(p, torch, stream, dev):
         p.thiim_set_coeffs(ctx, co64)
         p.thiim_set_fields(ctx, f64)
         it64, r64 = 0, 1.0
-        while it64 < 400000 and r64 > 1e-11:
-            p.thiim_iterate(ctx, 2000)
-            it64 += 2000
+        while it64 < 300000 and r64 > 1e-11:
+            p.thiim_iterate(ctx, 2500)
+            it64 += 2500
             r64 = p.thiim_residual(ctx)
     finally:
         p.thiim_destroy(ctx)
@@ -391,7 +393,8 @@ def _variant_mixed_accuracy(p, torch, stream, dev):
         p.thiim_set_tuning(ctx, 1, 4)
         p.thiim_set_coeffs(ctx, co32)
         p.thiim_set_fields(ctx, work)
-        outer, rm = p.thiim_mixed_solve(ctx, co64, x64, 50, 2000, 1e-7)
+        # to the mixed solver's FP64-residual floor (about 5e-8 here): 2000 outer steps
+        outer, rm = p.thiim_mixed_solve(ctx, co64, x64, 50, 2000, 1e-9)
     finally:
         p.thiim_destroy(ctx)
     torch.cuda.synchronize()
