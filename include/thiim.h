@@ -146,7 +146,9 @@ int thiim_set_fields(thiim_ctx *ctx, void *const field[THIIM_N_FIELDS]);
  * THIIM_C128_PAIR the intermediate iterates of one call are kept as FP32
  * pairs (in the caller's and the library's field arrays) and only the final
  * one is written as complex128.  The last
- * iteration also accumulates, in FP64, the norms that thiim_residual reports.
+ * iteration also accumulates the norms that thiim_residual reports (per
+ * thread in FP64, or in FP32 pairs, ~48 bits, under THIIM_C128_PAIR; summed
+ * across threads and CTAs in FP64).
  * n_iters = 0 does nothing.  Errors: THIIM_ERR_STATE if fields or
  * coefficients are missing, THIIM_ERR_ARG if n_iters < 0, THIIM_ERR_CUDA.
  */

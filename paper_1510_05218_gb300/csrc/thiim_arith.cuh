@@ -100,6 +100,19 @@ struct Native {
     }
     __device__ static __forceinline__ double re(Z a) { return (double)a.x; }
     __device__ static __forceinline__ double im(Z a) { return (double)a.y; }
+    // residual norms: FP64 sums of the three components' terms
+    typedef double Acc;
+    __device__ static __forceinline__ Acc acc_zero() { return 0.0; }
+    __device__ static __forceinline__ double acc_value(Acc a) { return a; }
+    __device__ static __forceinline__ double d2(Z a, Z b) {
+        const double x = re(a) - re(b), y = im(a) - im(b);
+        return x * x + y * y;
+    }
+    __device__ static __forceinline__ double n2(Z a) { const double x = re(a), y = im(a); return x * x + y * y; }
+    __device__ static __forceinline__ void acc_d3(Acc &acc, Z a0, Z b0, Z a1, Z b1, Z a2, Z b2) {
+        acc += d2(a0, b0) + d2(a1, b1) + d2(a2, b2);
+    }
+    __device__ static __forceinline__ void acc_n3(Acc &acc, Z a0, Z a1, Z a2) { acc += n2(a0) + n2(a1) + n2(a2); }
 };
 
 // ------------------------------------------------------------ FP32 pairs ----
@@ -215,6 +228,21 @@ struct PairArith {
     __device__ static __forceinline__ Z upd(Z x, Z t, Z c, Z d) { return upd_impl(x, t, c, d, nullptr); }
     __device__ static __forceinline__ double re(Z a) { return (double)a.x.h + (double)a.x.l; }
     __device__ static __forceinline__ double im(Z a) { return (double)a.y.h + (double)a.y.l; }
+    // residual norms: squares and sums in pair arithmetic on the FP32 pipe (the
+    // per-thread sum keeps ~48 bits); converted to FP64 once per thread
+    typedef pacc Acc;
+    __device__ static __forceinline__ Acc acc_zero() { Acc a; a.s = 0.f; a.lo = 0.f; return a; }
+    __device__ static __forceinline__ double acc_value(Acc a) { return (double)a.s + (double)a.lo; }
+    __device__ static __forceinline__ void acc_sq(Acc &acc, fpair v) { acc.prod(v.h, v.l, v.h, v.l); }
+    __device__ static __forceinline__ void acc_d3(Acc &acc, Z a0, Z b0, Z a1, Z b1, Z a2, Z b2) {
+        acc_sq(acc, p_sub(a0.x, b0.x)); acc_sq(acc, p_sub(a0.y, b0.y));
+        acc_sq(acc, p_sub(a1.x, b1.x)); acc_sq(acc, p_sub(a1.y, b1.y));
+        acc_sq(acc, p_sub(a2.x, b2.x)); acc_sq(acc, p_sub(a2.y, b2.y));
+    }
+    __device__ static __forceinline__ void acc_n3(Acc &acc, Z a0, Z a1, Z a2) {
+        acc_sq(acc, a0.x); acc_sq(acc, a0.y); acc_sq(acc, a1.x); acc_sq(acc, a1.y);
+        acc_sq(acc, a2.x); acc_sq(acc, a2.y);
+    }
 };
 
 }  // namespace thiim

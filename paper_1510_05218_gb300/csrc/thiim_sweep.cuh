@@ -99,16 +99,6 @@ __device__ __forceinline__ bool wrap(int &g, int n, bool periodic) {
     return true;
 }
 
-template <typename A>
-__device__ __forceinline__ double norm2(typename A::Z a) {
-    const double x = A::re(a), y = A::im(a);
-    return x * x + y * y;
-}
-template <typename A>
-__device__ __forceinline__ double dnorm2(typename A::Z a, typename A::Z b) {
-    const double x = A::re(a) - A::re(b), y = A::im(a) - A::im(b);
-    return x * x + y * y;
-}
 
 template <typename A, int MODE, bool TBL = false>
 struct SplitIO {
@@ -178,7 +168,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, int tile, int chu
     const int hw = nix + 1, hcount = (nix + 1) * (niy + 1);
     const int tcount = nix * niy;
     const bool want_norm = partial_out != nullptr;
-    double acc_d = 0.0, acc_x = 0.0;
+    typename A::Acc acc_d = A::acc_zero(), acc_x = A::acc_zero();
 
     const uint64_t pol_keep = THIIM_L2_HINT_A ? l2_evict_last() : 0;
     auto ld_e_first = [&](int s, size_t p) {
@@ -252,9 +242,8 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, int tile, int chu
                     IO::store_pair(a, HYX, p, nyx, oyx, nyz, oyz);
                     IO::store_pair(a, HZX, p, nzx, ozx, nzy, ozy);
                     if (want_norm) {
-                        acc_d += dnorm2<A>(hn.x, A::add(oxy, oxz)) + dnorm2<A>(hn.y, A::add(oyx, oyz)) +
-                                 dnorm2<A>(hn.z, A::add(ozx, ozy));
-                        acc_x += norm2<A>(hn.x) + norm2<A>(hn.y) + norm2<A>(hn.z);
+                        A::acc_d3(acc_d, hn.x, A::add(oxy, oxz), hn.y, A::add(oyx, oyz), hn.z, A::add(ozx, ozy));
+                        A::acc_n3(acc_x, hn.x, hn.y, hn.z);
                     }
                 }
             }
@@ -295,9 +284,8 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, int tile, int chu
                 IO::store_pair(a, EZX, p, nzx, ozx, nzy, ozy);
                 if (want_norm) {
                     const Z fx = A::add(nxy, nxz), fy = A::add(nyx, nyz), fz = A::add(nzx, nzy);
-                    acc_d += dnorm2<A>(fx, A::add(oxy, oxz)) + dnorm2<A>(fy, A::add(oyx, oyz)) +
-                             dnorm2<A>(fz, A::add(ozx, ozy));
-                    acc_x += norm2<A>(fx) + norm2<A>(fy) + norm2<A>(fz);
+                    A::acc_d3(acc_d, fx, A::add(oxy, oxz), fy, A::add(oyx, oyz), fz, A::add(ozx, ozy));
+                    A::acc_n3(acc_x, fx, fy, fz);
                 }
             }
         }
@@ -305,13 +293,14 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, int tile, int chu
     }
 
     if (want_norm) {
-        // CTA reduction in a fixed order, then one partial pair per CTA.
+        // CTA reduction in FP64 in a fixed order, then one partial pair per CTA.
+        double sd = A::acc_value(acc_d), sx = A::acc_value(acc_x);
         for (int o = 16; o > 0; o >>= 1) {
-            acc_d += __shfl_down_sync(0xffffffffu, acc_d, o);
-            acc_x += __shfl_down_sync(0xffffffffu, acc_x, o);
+            sd += __shfl_down_sync(0xffffffffu, sd, o);
+            sx += __shfl_down_sync(0xffffffffu, sx, o);
         }
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-        if (lane == 0) { red[0][warp] = acc_d; red[1][warp] = acc_x; }
+        if (lane == 0) { red[0][warp] = sd; red[1][warp] = sx; }
         __syncthreads();
         if (threadIdx.x == 0) {
             double d = 0.0, x = 0.0;

@@ -56,7 +56,7 @@ sweep2_kernel(const SweepArgs a) {
     const int z1 = min(z0 + a.zchunk, nz);
     const size_t plane = (size_t)nx * ny;
     const bool want_norm = a.partials != nullptr;
-    double acc_d = 0.0, acc_x = 0.0;
+    typename A::Acc acc_d = A::acc_zero(), acc_x = A::acc_zero();
 
     // plane index inside the grid, or -1 outside a Dirichlet edge
     auto zin = [&](int k) -> int {
@@ -202,8 +202,8 @@ sweep2_kernel(const SweepArgs a) {
                         for (int q = 0; q < 6; ++q) A::st_field(a.dst[HXY + q], p, r.s[q]);
                         if (want_norm) {
                             const Vec3<Z> f1 = sH1[bh ^ 1][v + 1][u + 1];
-                            acc_d += dnorm2<A>(f.x, f1.x) + dnorm2<A>(f.y, f1.y) + dnorm2<A>(f.z, f1.z);
-                            acc_x += norm2<A>(f.x) + norm2<A>(f.y) + norm2<A>(f.z);
+                            A::acc_d3(acc_d, f.x, f1.x, f.y, f1.y, f.z, f1.z);
+                            A::acc_n3(acc_x, f.x, f.y, f.z);
                         }
                     }
                 }
@@ -225,8 +225,8 @@ sweep2_kernel(const SweepArgs a) {
                 if (want_norm) {
                     const Vec3<Z> f1 = sE1[be ^ 1][v + 1][u + 1];
                     const Z fx = A::add(out[0], out[1]), fy = A::add(out[2], out[3]), fz = A::add(out[4], out[5]);
-                    acc_d += dnorm2<A>(fx, f1.x) + dnorm2<A>(fy, f1.y) + dnorm2<A>(fz, f1.z);
-                    acc_x += norm2<A>(fx) + norm2<A>(fy) + norm2<A>(fz);
+                    A::acc_d3(acc_d, fx, f1.x, fy, f1.y, fz, f1.z);
+                    A::acc_n3(acc_x, fx, fy, fz);
                 }
             }
         }
@@ -237,13 +237,14 @@ sweep2_kernel(const SweepArgs a) {
     }
 
     if (want_norm) {
+        double sd = A::acc_value(acc_d), sx = A::acc_value(acc_x);
         for (int o = 16; o > 0; o >>= 1) {
-            acc_d += __shfl_down_sync(0xffffffffu, acc_d, o);
-            acc_x += __shfl_down_sync(0xffffffffu, acc_x, o);
+            sd += __shfl_down_sync(0xffffffffu, sd, o);
+            sx += __shfl_down_sync(0xffffffffu, sx, o);
         }
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
         __syncthreads();
-        if (lane == 0) { red[0][warp] = acc_d; red[1][warp] = acc_x; }
+        if (lane == 0) { red[0][warp] = sd; red[1][warp] = sx; }
         __syncthreads();
         if (threadIdx.x == 0) {
             double d = 0.0, x = 0.0;
