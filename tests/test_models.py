@@ -55,3 +55,33 @@ def test_candidates_respect_the_model():
     c = tuning.candidates(1, 512, 1024, 152, 129 * 2 ** 20)
     assert (1, 64) in c and any(t == 2 for t, _ in c)
     assert all(t == 1 for t, _ in tuning.candidates(0, 512, 1024, 152, 129 * 2 ** 20))
+
+
+def test_footprint_model_matches_the_kernels_shared_memory():
+    """The footprint model's shared memory per CTA equals what ptxas reports for
+    the sweep kernels (plus the 2 x NT/32 doubles of the norm reduction)."""
+    import concurrent.futures as cf
+    import re
+    import shutil
+    import subprocess
+
+    from paper_1510_05218_gb300 import build
+
+    nvcc = build._nvcc()
+    if shutil.which(nvcc) is None and not os.path.exists(nvcc):
+        pytest.skip("nvcc not available")
+    cases = [("thiim_sweep_f64.cu", 0, 1, 256), ("thiim_sweep_f32.cu", 1, 1, 256),
+             ("thiim_sweep_pair_b.cu", 2, 1, 256), ("thiim_sweep2_f32.cu", 1, 2, 512)]
+
+    def smem(src):
+        cmd = [nvcc, *build.ARCH, "-O3", "-std=c++17", "-I", build.INCLUDE, "-I", build.CSRC, "-Xptxas", "-v",
+               "-cubin", "-o", os.devnull, os.path.join(build.CSRC, src)]
+        out = subprocess.run(cmd, capture_output=True, text=True, timeout=600)
+        assert out.returncode == 0, out.stderr[-2000:]
+        return {int(v) for v in re.findall(r"(\d+) bytes smem", out.stderr)}
+
+    with cf.ThreadPoolExecutor(4) as ex:
+        found = list(ex.map(lambda c: smem(c[0]), cases))
+    for (src, precision, temporal, nt), sizes in zip(cases, found):
+        model = tuning.gpu_footprint(precision, temporal, 32, 8192, 152, 129 * 2 ** 20)["smem_per_cta"]
+        assert sizes == {model + 2 * (nt // 32) * 8}, (src, sizes, model)
