@@ -252,7 +252,8 @@ int thiim_absorbed_power(thiim_ctx *ctx, const double *sigma, double *power);
  *            coefficient order of thiim_set_coeffs.  Owned by the caller.
  * Synchronises the stream.  Errors: THIIM_ERR_ARG (as thiim_build_coeffs;
  * also n_mat out of range or a zero or non-finite permittivity),
- * THIIM_ERR_ALIGN, THIIM_ERR_NOMEM, THIIM_ERR_CUDA.
+ * THIIM_ERR_ALIGN, THIIM_ERR_NOMEM, THIIM_ERR_CUDA.  n_mat * nz above 2^31 - 1
+ * is rejected with THIIM_ERR_ARG.
  */
 int thiim_build_material_table(thiim_ctx *ctx, int n_mat, const double *eps_mat,
                                const double *sigma_pml_e, const double *sigma_pml_h,

@@ -502,6 +502,7 @@ int thiim_build_material_table(thiim_ctx *c, int n_mat, const double *eps_mat, c
                                const double *sigma_pml_h, double omega, double tau, int k_s,
                                const double jones[4], void *table) {
     if (!c || !eps_mat || !table || !jones || n_mat < 1 || n_mat > THIIM_MAX_MATERIALS) return THIIM_ERR_ARG;
+    if ((long long)n_mat * c->nz > 0x7FFFFFFFLL) return THIIM_ERR_ARG;   // table rows are indexed as int
     if (!aligned(table, c->elem)) return THIIM_ERR_ALIGN;
     for (int m = 0; m < 2 * n_mat; ++m)
         if (!isfinite(eps_mat[m])) return THIIM_ERR_ARG;
