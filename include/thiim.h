@@ -150,7 +150,9 @@ int thiim_set_fields(thiim_ctx *ctx, void *const field[THIIM_N_FIELDS]);
  * thread in FP64, or in FP32 pairs, ~48 bits, under THIIM_C128_PAIR; summed
  * across threads and CTAs in FP64).
  * n_iters = 0 does nothing.  Errors: THIIM_ERR_STATE if fields or
- * coefficients are missing, THIIM_ERR_ARG if n_iters < 0, THIIM_ERR_CUDA.
+ * coefficients are missing, THIIM_ERR_ARG if n_iters < 0 or the grid needs
+ * more CTAs than one launch takes (2^31 - 1 tiles, or 65535 z chunks: raise
+ * zchunk with thiim_set_tuning), THIIM_ERR_CUDA.
  */
 int thiim_iterate(thiim_ctx *ctx, int n_iters);
 

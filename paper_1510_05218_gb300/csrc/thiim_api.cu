@@ -357,6 +357,8 @@ int thiim_iterate(thiim_ctx *c, int n_iters) {
     if (n_iters == 0) return THIIM_OK;
     const int tx = tiles_x(c), ty = tiles_y(c);
     const int chunks = (c->nz + c->zchunk - 1) / c->zchunk;
+    // one CTA per (tile, z chunk): the launch's grid limits (x < 2^31, y <= 65535)
+    if ((long long)tx * ty > 0x7FFFFFFFLL || chunks > 65535) return THIIM_ERR_ARG;
     const dim3 grid((unsigned)(tx * ty), (unsigned)chunks);
     const size_t ctas = (size_t)tx * ty * chunks;
     int st = ensure_partials(c, ctas);
