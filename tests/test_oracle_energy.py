@@ -85,3 +85,14 @@ def test_incident_flux_of_the_discrete_plane_wave():
     for k in (9, 13, 20):
         flux = (np.conj(e_inc(k - 1)) * h_inc(k)).real
         assert abs(0.5 * flux - 0.5 * abs(amp) ** 2 * math.sin(kappa) / wt) <= 1e-14
+
+
+def test_spectrum_incident_power_is_the_plane_wave_flux():
+    """The spectrum driver's incident power (product code, host arithmetic)
+    equals the discrete plane wave's time-averaged flux over a plane of faces."""
+    from paper_1510_05218_gb300.spectrum import incident_power
+    for lam, tau, amp in ((20.0, 0.5, 1.0), (33.0, 0.4, 0.3 + 0.7j), (80.0, 0.5, 2.0)):
+        omega = 2 * math.pi / lam
+        e_inc, h_inc = incident_wave(omega, tau, 5, amp)
+        flux = 0.5 * (np.conj(e_inc(9)) * h_inc(10)).real          # one face, E plane 9 / H plane 10
+        assert abs(incident_power(omega, tau, 7, 3, amp) - 21 * flux) <= 1e-13 * abs(21 * flux)
