@@ -42,3 +42,12 @@ def test_no_cpu_fallback_in_the_product_package():
     for f in pkg.rglob("*.py"):
         text = f.read_text()
         assert "import oracle" not in text and "from oracle" not in text, f
+
+
+def test_every_declared_call_has_a_python_binding():
+    """The binding mirrors the ABI: each call declared in include/thiim.h is
+    wrapped under the same name in paper_1510_05218_gb300.thiim."""
+    import paper_1510_05218_gb300.thiim as T
+    names = T.declared_symbols()
+    missing = [n for n in names if not callable(getattr(T, n, None))]
+    assert not missing, missing
