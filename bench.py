@@ -3,11 +3,16 @@
 Workload (default): the 512^3 textured thin-film stack in complex128 — 12
 split fields + 28 coefficient arrays, 86 GB resident in HBM — with the
 plane-wave source; one step = thiim_iterate(200) followed by thiim_residual
-(the FP64 relative update of the last iteration).  The headline path keeps
-complex128 data and computes on FP32 pairs (GB300's FP64 rate caps the
-native FP64 sweep near 43 % of the HBM roofline); "variants" reports native
-FP64, complex64, mixed precision with FP64 defect correction and the
-32-solve batch, each measured after one warm-up.  MLUP/s = cells x
+(the FP64 relative update of the last iteration).  The headline computes in
+FP64 (dtype f64), the paper's arithmetic.  GB300 executes FP64 at a small
+fraction of its FP32 rate, so the line carries two rooflines for the sweep:
+the FP64 pipe (instructions per cell against the pipe rate measured in the
+same run) and HBM (832 algorithmic bytes per cell against the measured copy
+bandwidth).  "variants" (the last key, numbers only) reports the other
+arithmetic of the same data and the other configurations: FP32-pair
+arithmetic on complex128 data, complex64, temporal blocking, the material
+table, mixed precision with FP64 defect correction, the 32-solve batch, the
+spectrum and the adjoint, each measured after one warm-up.  MLUP/s = cells x
 iterations / time.  Every input array is larger than L2, so no flush is
 needed between steps.
 
@@ -38,12 +43,24 @@ DTYPE = {"c128": "f64", "pair": "f32x2", "c64": "f32"}
 PRECISION_CODE = {"c128": 0, "c64": 1, "pair": 2}
 KERNEL = {"c128": "sweep_kernel<Native<double>>", "pair": "sweep_kernel<PairArith<1,1>>",
           "c64": "sweep_kernel<Native<float>>"}
+# FP64 pipe instructions (DFMA, DADD, DMUL) per cell and iteration of the
+# sweep's arithmetic without halo recomputation: per split 8 multiply-adds for
+# t x + c D (+ Src) and 2 adds for the difference, plus 2 adds per full
+# component sum (12 splits, 6 components): 12 * 10 + 6 * 2 = 132.
+FP64_INSTR_PER_LUP = 132
 PRECISION_NOTE = {"c128": "with native FP64 arithmetic",
                   "pair": "with FP32-pair arithmetic (parity with the FP64 oracle <= 1e-12)",
                   "c64": "stored as complex64 with FP32 arithmetic"}
 FLOPS_PER_LUP = 248                                  # the paper's count (Sec. III-A)
 SWEEP_SRC = [os.path.join(ROOT, "paper_1510_05218_gb300", "csrc", f) for f in ("thiim_sweep.cuh", "thiim_internal.h")]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "sweep_traffic.json")
+
+
+def _sig(x, n=4):
+    """x rounded to n significant digits (keeps the JSON line short)."""
+    if x is None or x == 0 or x != x:
+        return x
+    return float("%.*g" % (n, x))
 
 
 def _dist():
@@ -188,11 +205,13 @@ def run_reference(args):
     st = stack_config(args.workload)
     threads = os.cpu_count() or 1
     planes = args.ref_planes
-    rates = []
+    rates, step_ms = [], []
     for _ in range(args.warmup):
         cpu_oracle_rate(st, planes, 2.0, threads)
     for _ in range(args.steps):
+        t0 = time.perf_counter()
         r, info = cpu_oracle_rate(st, planes, args.ref_seconds, threads)
+        step_ms.append((time.perf_counter() - t0) * 1e3)
         rates.append(r)
     value = statistics.median(rates)
     sample = ("oracle (plain C, OpenMP over z) on a %dx%dx%d slab (planes %d-%d) of the %s workload, "
@@ -200,10 +219,12 @@ def run_reference(args):
                                                     args.workload, info["iters"], info["seconds"]))
     out = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "MLUP/s", "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": args.ref_seconds * 1000.0,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.median(step_ms),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": "%s: %dx%dx%d textured thin-film stack, complex128" % (args.workload, st.nx, st.ny, st.nz),
-                   "parallelism": "host cores"},
+                   "parallelism": "host cores",
+                   "sample": "each step times a %d-plane slab of the full grid (the oracle at the full size "
+                             "would take minutes per iteration); MLUP/s counts the slab's cells" % planes},
         "cpu_baseline": {"value": value, "unit": "MLUP/s", "cores": threads, "kind": "oracle", "sample": sample,
                          "cpu_model": _cpu_model()},
         "e2e": {"value": value, "unit": "MLUP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -301,18 +322,9 @@ def _variant_sweep(p, torch, st, precision, stream, dev, iters, warmup, steps, p
     achieved = alg * cells / launch_s / 1e9
     del co, fields, eps
     torch.cuda.empty_cache()
-    kernel = KERNEL[precision] if temporal == 1 else "sweep2_kernel<Native<float>> (2 iterations/launch)"
-    if table:
-        kernel = kernel[:-1] + ", table>"
-    return {"value": cells * iters * steps / (ms_total / 1e3) / 1e6, "unit": "MLUP/s", "dtype": DTYPE[precision],
-            "kernel": kernel, "alg_bytes_per_lup": alg,
-            "coefficients": ("material map (1 B/cell) + (material, plane) table: a variant, not the paper's "
-                             "28-array layout" if table else "28 arrays"),
-            "launch_ms": launch_s * 1e3 * temporal, "achieved_gbs": achieved,
-            "frac_hbm": achieved / peak, "residual_last": res[-1], "steps": steps, "warmup": warmup,
-            "iterations_per_launch": temporal, "tuning": list(choice) if choice else None,
-            "note": "achieved_gbs counts the single-iteration algorithmic bytes per LUP (an effective rate "
-                    "for temporal blocking, which moves fewer DRAM bytes)" if temporal != 1 else ""}
+    return {"value": _sig(cells * iters * steps / (ms_total / 1e3) / 1e6), "dtype": DTYPE[precision],
+            "frac_hbm": _sig(achieved / peak, 3), "launch_ms": _sig(launch_s * 1e3 * temporal),
+            "residual": _sig(res[-1], 3), "tuning": list(choice) if choice else None}
 
 
 def _variant_mixed(p, torch, st, stream, dev, inner, outer, warmup):
@@ -348,10 +360,8 @@ def _variant_mixed(p, torch, st, stream, dev, inner, outer, warmup):
     cells = st.nx * st.ny * st.nz
     del co64, co32, work, x64
     torch.cuda.empty_cache()
-    return {"value": cells * inner * done / (ms / 1e3) / 1e6, "unit": "MLUP/s", "dtype": "f32+f64",
-            "inner_iters": inner, "outer": done, "fp64_defects": done + 1, "residual_last": r,
-            "what": "MLUP/s counts the %d complex64 iterations per outer step; each outer step also runs one "
-                    "FP64 defect sweep and a fold" % inner}
+    return {"value": _sig(cells * inner * done / (ms / 1e3) / 1e6), "dtype": "f32+f64", "inner": inner,
+            "residual": _sig(r, 3)}
 
 
 def _variant_mixed_accuracy(p, torch, stream, dev):
@@ -403,11 +413,8 @@ def _variant_mixed_accuracy(p, torch, stream, dev):
         ref = f64[2 * c] + f64[2 * c + 1]
         mix = x64[2 * c] + x64[2 * c + 1]
         errs.append(float(torch.linalg.vector_norm(mix - ref) / torch.linalg.vector_norm(ref)))
-    return {"max_rel_err_full_components": max(errs), "bound": 1e-6, "within_bound": max(errs) <= 1e-6,
-            "fp64_iterations": it64, "fp64_residual": r64, "mixed_outer_steps": outer, "mixed_fp64_residual": rm,
-            "seconds": time.perf_counter() - t0,
-            "what": "32^3 stack converged on the GPU by native FP64 and by thiim_mixed_solve (50 complex64 "
-                    "iterations per FP64 defect); relative L2 difference of the six full components"}
+    return {"max_rel_err": _sig(max(errs), 3), "bound": 1e-6, "grid": 32, "fp64_residual": _sig(r64, 2),
+            "mixed_residual": _sig(rm, 2)}
 
 
 def _variant_batch(p, torch, precision, stream, dev, iters, check, warmup):
@@ -432,11 +439,8 @@ def _variant_batch(p, torch, precision, stream, dev, iters, check, warmup):
             p.thiim_destroy(c)
     del probs
     torch.cuda.empty_cache()
-    return {"value": cells * iters / (ms / 1e3) / 1e6, "unit": "MLUP/s", "dtype": DTYPE[precision],
-            "solves": len(stacks), "cells_total": cells, "iters": iters, "check_every": check,
-            "grids": "Nx=Ny in [%d, %d], Nz in [%d, %d]" % (min(s.nx for s in stacks), max(s.nx for s in stacks),
-                                                          min(s.nz for s in stacks), max(s.nz for s in stacks)),
-            "residual_max": max(res)}
+    return {"value": _sig(cells * iters / (ms / 1e3) / 1e6), "dtype": DTYPE[precision], "iters": iters,
+            "residual_max": _sig(max(res), 3)}
 
 
 def _variant_spectrum(p, torch, precision, n_lambda, iters):
@@ -457,12 +461,8 @@ def _variant_spectrum(p, torch, precision, n_lambda, iters):
     torch.cuda.empty_cache()
     cells = st.nx * st.ny * st.nz
     solves = 2 * n_lambda
-    return {"value": solves * cells * iters / dt / 1e6, "unit": "MLUP/s", "dtype": DTYPE[precision],
-            "solves": solves, "iterations_each": iters, "seconds": dt,
-            "what": "%d wavelengths x 2 polarisations of the 128^3 stack in one thiim_batch_iterate call; "
-                    "wall clock incl. coefficient builds and absorbed-power reductions" % n_lambda,
-            "A_unpolarised_first_last": [r["A_unpolarised"][0], r["A_unpolarised"][-1]],
-            "residual_max": max(r["residuals"])}
+    return {"value": _sig(solves * cells * iters / dt / 1e6), "dtype": DTYPE[precision], "solves": solves,
+            "A_first_last": [_sig(r["A_unpolarised"][0]), _sig(r["A_unpolarised"][-1])]}
 
 
 def _variant_adjoint_steady(p, torch, stream, dev, terms, peak):
@@ -491,11 +491,8 @@ def _variant_adjoint_steady(p, torch, stream, dev, terms, peak):
     cells = st.nx * st.ny * st.nz
     # per term and cell: lam, lh, the running sum and the t, c arrays read; lam, lh, the sum written
     alg = (12 + 6 + 12 + 24) * 16 + (12 + 6 + 12) * 16
-    return {"value": cells * terms / (ms / 1e3) / 1e6, "unit": "MLUP/s (adjoint terms)", "dtype": "f64",
-            "terms": terms, "ms": ms, "alg_bytes_per_term": alg,
-            "frac_hbm": cells * terms * alg / (ms / 1e3) / 1e9 / peak,
-            "what": "thiim_adjoint_steady at 128^3: propagation kernels (FP64 gather, one thread per cell) "
-                    "and one gradient evaluation"}
+    return {"value": _sig(cells * terms / (ms / 1e3) / 1e6), "dtype": "f64",
+            "frac_hbm": _sig(cells * terms * alg / (ms / 1e3) / 1e9 / peak, 3)}
 
 
 def run_grid_sweep(args):
@@ -581,6 +578,8 @@ def run_ours(args):
         p.thiim_iterate(ctx, iters)
         p.thiim_residual(ctx)
     torch.cuda.synchronize()
+    # the FP64 pipe's measured rate, right after the warm-up (same clocks)
+    fp64_rate = p.thiim_fp64_pipe_rate(stream) if args.precision == "c128" else None
     sampler = ClockSampler(_clock_index(local))
     sampler.start()
     time.sleep(0.3)
@@ -598,6 +597,21 @@ def run_ours(args):
     achieved = alg_per_lup * cells / launch_s / 1e9
     kernel_key = KERNEL[args.precision][:-1] + ", table>" if table else KERNEL[args.precision]
     traffic = _traffic(kernel_key, cells)
+    hbm = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+           "traffic": traffic, "peak_kind": peak_kind, "kernel": kernel_key, "alg_bytes_per_lup": alg_per_lup,
+           "launch_ms": launch_s * 1e3}
+    if fp64_rate:
+        # FP64 arithmetic: the sweep is bound by the FP64 pipe, not by HBM
+        achieved_fp64 = FP64_INSTR_PER_LUP * cells / launch_s / 1e9
+        roofline = {"bound": "fp64_pipe", "achieved": achieved_fp64, "peak": fp64_rate / 1e9,
+                    "unit": "G FP64 instr/s", "frac": achieved_fp64 * 1e9 / fp64_rate, "traffic": traffic,
+                    "peak_kind": "measured in this run (thiim_fp64_pipe_rate: DFMA throughput, all SMs)",
+                    "kernel": kernel_key, "alg_fp64_instr_per_lup": FP64_INSTR_PER_LUP,
+                    "launch_ms": launch_s * 1e3,
+                    "hbm": {k: hbm[k] for k in ("achieved", "peak", "unit", "frac", "peak_kind",
+                                                "alg_bytes_per_lup")}}
+    else:
+        roofline = hbm
 
     # --- end to end through the public API with host buffers --------------
     e2e = None
@@ -644,17 +658,20 @@ def run_ours(args):
 
     variants = {}
     if not args.no_variants:
-        for mode in ("c128", "pair", "c64"):
+        # FP32-pair arithmetic on the same complex128 data first: FP64-accurate
+        # (1e-12 parity with the oracle), narrower exponent range than FP64
+        for mode in ("pair", "c128", "c64"):
             if mode != args.precision:
                 variants[mode] = _variant_sweep(p, torch, st, mode, stream, dev, iters, 1, 1, peak)
         variants["c64_temporal2"] = _variant_sweep(p, torch, st, "c64", stream, dev, iters, 1, 1, peak, temporal=2)
         for mode in ("pair", "c64"):
-            variants[mode + "_material_table"] = _variant_sweep(p, torch, st, mode, stream, dev, iters, 1, 1, peak,
-                                                               table=True)
-        variants["mixed_c64_f64_defect"] = _variant_mixed(p, torch, st, stream, dev, 50, 4, 1)
-        variants["mixed_c64_f64_defect"]["accuracy_vs_fp64"] = _variant_mixed_accuracy(p, torch, stream, dev)
-        variants["batch32_" + args.precision] = _variant_batch(p, torch, args.precision, stream, dev, 200, 50, 1)
-        variants["spectrum16x2_" + args.precision] = _variant_spectrum(p, torch, args.precision, 16, 200)
+            variants[mode + "_table"] = _variant_sweep(p, torch, st, mode, stream, dev, iters, 1, 1, peak,
+                                                       table=True)
+        variants["mixed"] = _variant_mixed(p, torch, st, stream, dev, 50, 4, 1)
+        variants["mixed"]["accuracy"] = _variant_mixed_accuracy(p, torch, stream, dev)
+        bprec = "pair" if args.precision == "c128" else args.precision
+        variants["batch32"] = _variant_batch(p, torch, bprec, stream, dev, 200, 50, 1)
+        variants["spectrum16x2"] = _variant_spectrum(p, torch, bprec, 16, 200)
         variants["adjoint_steady_128"] = _variant_adjoint_steady(p, torch, stream, dev, 200, peak)
 
     if rank != 0:
@@ -686,16 +703,18 @@ def run_ours(args):
                    "tuning": tuning_info,
                    "l2": "inputs larger than L2 (no flush needed)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                     "kernel": kernel_key, "alg_bytes_per_lup": alg_per_lup,
-                     "launch_ms": launch_s * 1e3},
+        "roofline": roofline,
         "gflops_paper_count": value * FLOPS_PER_LUP / 1e3,
         "residual_last": residuals[-1] if residuals else None,
         "clocks": clocks,
         "e2e": e2e,
         "gpu_launches": args.steps * (iters + 1),
         "cpu_baseline": cpu,
+        "variants_legend": ("MLUP/s of the same 512^3 stack in other arithmetic (pair: FP32 pairs on complex128 "
+                            "data, 1e-12 oracle parity; c64: complex64), with 2 iterations per launch, with "
+                            "material-table coefficients, mixed c64 + FP64 defect (accuracy: 32^3 converged, vs "
+                            "FP64), 32 uneven batched solves, a 16x2 spectrum and the steady adjoint at 128^3; "
+                            "frac_hbm uses the single-iteration algorithmic bytes"),
         "variants": variants,
     }
     print(json.dumps(out), flush=True)
@@ -711,7 +730,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="stack512")
-    ap.add_argument("--precision", default="pair", choices=["c128", "pair", "c64"])
+    ap.add_argument("--precision", default="c128", choices=["c128", "pair", "c64"])
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--coeffs", default="arrays", choices=["arrays", "table"],
                     help="table: material-id map + (material, plane) table (a variant, not the headline layout)")

@@ -423,9 +423,11 @@ int thiim_batch_iterate(thiim_ctx *const ctx[], int nb, int max_iters, int check
  *   Scratch: the reduction partials live in one fixed device array of
  *   16384 CTAs x 16 B (+16 B) = 256 KiB, defined in the library and held by
  *   every GPU that loads it until the process exits.  A grid needing more
- *   than 16384 CTAs of 32 x 8 cells (nx/32 * ny/8 > 16384) is rejected with
- *   THIIM_ERR_ARG.  The first call on a device looks up the array's device
- *   address; make that first call before any stream capture.  All calls
+ *   than 16384 CTAs of 32 x 8 cells (ceil(nx/32) * ceil(ny/8) > 16384) is
+ *   rejected with THIIM_ERR_ARG before anything is enqueued.  Each call with
+ *   a residual looks up the array's device address (the first lookup on a
+ *   device loads the library's device code: make that first call before any
+ *   stream capture).  All calls
  *   share the array, so calls whose GPU work overlaps (other streams or
  *   host threads on the same device) race on it.
  * Errors: THIIM_ERR_ARG, THIIM_ERR_ALIGN, THIIM_ERR_CUDA, THIIM_ERR_NONFINITE.
@@ -434,6 +436,23 @@ int thiim_step_noalloc(int nx, int ny, int nz, int precision, unsigned bc_flags,
                        void *const src[THIIM_N_FIELDS], void *const dst[THIIM_N_FIELDS],
                        void *const coeff[THIIM_N_COEFFS], void *cuda_stream,
                        double *rel_residual);
+
+/*
+ * thiim_fp64_pipe_rate — measure the FP64 fused multiply-add throughput of
+ * the current device (a measurement helper; the paper has no counterpart).
+ * GB300 runs FP64 at a small fraction of its FP32 rate, so the FP64 sweep can
+ * be bound by that pipe instead of by memory bandwidth (the paper's Eqs. 8-10
+ * model only memory); this gives the denominator of that roofline, measured
+ * at the clocks of the caller's run.  A grid of 8 CTAs per SM runs 8
+ * independent FMA chains per thread; the best of 5 timed launches on
+ * cuda_stream (a cudaStream_t) is reported.
+ *   fma_per_s: host double receiving FP64 FMA instructions per second,
+ *              device-wide (one FMA = one FP64 pipe slot; DADD and DMUL take
+ *              one slot each as well).
+ * Allocates and frees a few kilobytes; synchronises the stream.
+ * Errors: THIIM_ERR_ARG (NULL), THIIM_ERR_NOMEM, THIIM_ERR_CUDA.
+ */
+int thiim_fp64_pipe_rate(void *cuda_stream, double *fma_per_s);
 
 /* Release the context and its scratch (synchronises the stream first). */
 void thiim_destroy(thiim_ctx *ctx);

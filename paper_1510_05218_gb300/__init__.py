@@ -12,6 +12,6 @@ from .thiim import (  # noqa: F401
     thiim_create, thiim_set_stream, thiim_set_tuning, thiim_set_coeffs, thiim_set_fields, thiim_iterate,
     thiim_residual, thiim_build_coeffs, thiim_mixed_solve, thiim_batch_iterate, thiim_adjoint_iterate, thiim_adjoint_steady, thiim_build_coeffs_grad,
     thiim_build_material_table, thiim_set_material_coeffs, thiim_build_coeffs_jones, thiim_absorbed_power,
-    thiim_step_noalloc, thiim_destroy, thiim_strerror, thiim_version,
+    thiim_step_noalloc, thiim_fp64_pipe_rate, thiim_destroy, thiim_strerror, thiim_version,
     Solver,
 )

@@ -17,8 +17,6 @@
 #include <math.h>
 #include <string.h>
 
-#include <mutex>
-
 #include "../../include/thiim.h"
 #include "thiim_internal.h"
 
@@ -32,26 +30,19 @@ constexpr size_t NOALLOC_MAX_CTAS = 16384;
 // partials[2*i], partials[2*i+1] for CTA i, then the two final norms.
 static __device__ __align__(256) double g_noalloc_scratch[2 * NOALLOC_MAX_CTAS + 2];
 
-constexpr int MAX_DEVICES = 64;
-std::mutex g_setup_mutex;
-double *g_scratch_addr[MAX_DEVICES];   // device address of g_noalloc_scratch, per device
-
-// Device address of the array on the current device, looked up once per
-// device.  The name g_noalloc_scratch in host code is only a host-side
-// handle; kernels must be given the address cudaGetSymbolAddress returns.
+// Device address of the array on the current device.  The name
+// g_noalloc_scratch in host code is only a host-side handle; kernels must be
+// given the address cudaGetSymbolAddress returns.  It is looked up on every
+// call that needs it (a host-side table lookup once the library's device code
+// is loaded), so a context that was reset and reloaded the module never sees
+// a stale address.  The first lookup on a device loads that code.
 int scratch_for_current_device(double **out) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) return THIIM_ERR_CUDA;
-    std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_addr[dev]) {
-        void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
-            cudaGetLastError();
-            return THIIM_ERR_CUDA;
-        }
-        g_scratch_addr[dev] = (double *)p;
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+        cudaGetLastError();
+        return THIIM_ERR_CUDA;
     }
-    *out = g_scratch_addr[dev];
+    *out = (double *)p;
     return THIIM_OK;
 }
 

@@ -90,6 +90,8 @@ def load_library(build_if_missing: bool = False):
     lib.thiim_build_material_table.restype = ctypes.c_int
     lib.thiim_set_material_coeffs.argtypes = [vp, vp, ctypes.c_int, vp]
     lib.thiim_set_material_coeffs.restype = ctypes.c_int
+    lib.thiim_fp64_pipe_rate.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
+    lib.thiim_fp64_pipe_rate.restype = ctypes.c_int
     lib.thiim_destroy.argtypes = [vp]
     lib.thiim_destroy.restype = None
     lib.thiim_strerror.argtypes = [ctypes.c_int]
@@ -303,6 +305,13 @@ def thiim_step_noalloc(nx, ny, nz, precision, bc_flags, src, dst, coeffs, stream
                                            ctypes.byref(r) if want_residual else None)
     _check("thiim_step_noalloc", rc)
     return r.value if want_residual else None
+
+
+def thiim_fp64_pipe_rate(stream=None) -> float:
+    """Measured FP64 FMA instructions per second of the current device."""
+    r = ctypes.c_double()
+    _check("thiim_fp64_pipe_rate", load_library().thiim_fp64_pipe_rate(_stream_ptr(stream), ctypes.byref(r)))
+    return r.value
 
 
 def thiim_destroy(ctx):
