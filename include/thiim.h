@@ -82,6 +82,13 @@ enum thiim_status {
     THIIM_ERR_NOMEM = -7      /* the library could not allocate its scratch */
 };
 
+/* Binary64 operations of the THIIM_C128 sweep that may run on the integer
+ * pipe (thiim_set_fp64_int_ops). */
+enum thiim_int_ops {
+    THIIM_INT_ADD = 1u,   /* additions and subtractions */
+    THIIM_INT_MUL = 2u    /* the leading product t * x of the updates without a source */
+};
+
 /* Number of field / coefficient arrays (Sec. III). */
 #define THIIM_N_FIELDS 12
 #define THIIM_N_COEFFS 28
@@ -119,6 +126,25 @@ int thiim_set_stream(thiim_ctx *ctx, void *cuda_stream);
  * Errors: THIIM_ERR_ARG.
  */
 int thiim_set_tuning(thiim_ctx *ctx, int temporal_block, int zchunk);
+
+/*
+ * thiim_set_fp64_int_ops — where the THIIM_C128 sweep of thiim_iterate
+ * computes its binary64 additions and multiplications (not in the paper; an
+ * execution choice for GB300).  Every update of Eqs. 3-5 is the same sequence
+ * of IEEE 754 binary64 operations (round to nearest even) whatever is chosen,
+ * so the results are bit-identical (NaN payloads aside).  GB300 retires
+ * FP64-pipe instructions at ~1.7 per SM and clock and integer instructions at
+ * 64-128, so the FP64 sweep is bound by its FP64 pipe; THIIM_INT_ADD computes
+ * the additions exactly in integer arithmetic instead (every operand pair,
+ * without branches), THIIM_INT_MUL the leading products (normal operands and
+ * results; the rest on the FP64 pipe).  The fused multiply-adds always use
+ * the FP64 pipe.  Measured on GB300 the sweep is not faster with either (an
+ * integer addition costs ~75 integer instructions), so the default is 0.
+ *   ops: 0 (everything on the FP64 pipe, the default), THIIM_INT_ADD, or
+ *        THIIM_INT_ADD | THIIM_INT_MUL.
+ * Errors: THIIM_ERR_ARG (not a THIIM_C128 context, other values).
+ */
+int thiim_set_fp64_int_ops(thiim_ctx *ctx, unsigned ops);
 
 /*
  * thiim_set_coeffs — borrow the 28 coefficient arrays (device pointers, in the

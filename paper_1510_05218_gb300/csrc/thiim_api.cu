@@ -285,6 +285,7 @@ int thiim_create(thiim_ctx **out, int nx, int ny, int nz, int precision, unsigne
     }
     c->zchunk = default_zchunk(c);
     c->temporal = 1;
+    c->fp64_int_ops = precision == THIIM_C128 ? THIIM_FP64_INT_OPS_DEFAULT : 0u;
     *out = c;
     return THIIM_OK;
 }
@@ -295,6 +296,13 @@ int thiim_set_tuning(thiim_ctx *c, int temporal_block, int zchunk) {
     if (temporal_block == 2 && c->precision != THIIM_C64) return THIIM_ERR_ARG;
     c->temporal = temporal_block;
     c->zchunk = zchunk ? zchunk : default_zchunk(c);
+    return THIIM_OK;
+}
+
+int thiim_set_fp64_int_ops(thiim_ctx *c, unsigned ops) {
+    if (!c || c->precision != THIIM_C128) return THIIM_ERR_ARG;
+    if (ops != 0u && ops != THIIM_INT_ADD && ops != (THIIM_INT_ADD | THIIM_INT_MUL)) return THIIM_ERR_ARG;
+    c->fp64_int_ops = ops;
     return THIIM_OK;
 }
 
@@ -433,6 +441,8 @@ int thiim_iterate(thiim_ctx *c, int n_iters) {
             e = launch_sweep_f32_tbl(a, grid, c->stream);
         else if (pair)   // intermediate iterates stay as float4 pairs; first reads and last writes complex128
             e = launch_sweep_pair(a, grid, c->stream, it > 0, it < n_iters - 1);
+        else if (c->precision == THIIM_C128 && c->fp64_int_ops)
+            e = launch_sweep_f64_int(a, grid, c->stream, (int)c->fp64_int_ops);
         else if (c->precision == THIIM_C128)
             e = launch_sweep_f64(a, grid, c->stream);
         else if (step == 2)

@@ -5,6 +5,9 @@
 //
 //   Native<double>  complex128 storage, FP64 arithmetic.
 //   Native<float>   complex64 storage, FP32 arithmetic.
+//   Fp64Int<OFF>    complex128 storage, FP64 arithmetic with part of it on
+//                   the integer pipe (thiim_i64f.cuh): bit-identical
+//                   results to Native<double>, fewer FP64-pipe instructions.
 //   PairArith<I,O>  complex128 data, arithmetic on pairs of FP32 numbers
 //                   (hi + lo, "double-float").  GB300 executes FP64 at
 //                   2 instructions/clk/SM but FP32 at 128, so the FP64 sweep
@@ -25,6 +28,8 @@
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include "thiim_i64f.cuh"
 
 namespace thiim {
 
@@ -113,6 +118,56 @@ struct Native {
         acc += d2(a0, b0) + d2(a1, b1) + d2(a2, b2);
     }
     __device__ static __forceinline__ void acc_n3(Acc &acc, Z a0, Z a1, Z a2) { acc += n2(a0) + n2(a1) + n2(a2); }
+};
+
+// ------------------------------------------- FP64 with integer-pipe ops ----
+// The FP64 sweep issues about 145 FP64-pipe instructions per cell (132 without
+// the halo): 86 fused multiply-adds, 41 additions (full-field sums and
+// differences) and 18 multiplications (the leading product t*x of the updates
+// without a source term).  GB300's FP64 pipe retires ~1.7 of them per SM and
+// clock, its integer units 64-128.  OFF selects which operations run as
+// integer-pipe binary64 arithmetic instead (thiim_i64f.cuh; bit 0: additions
+// and subtractions, bit 1: the leading products); the fused multiply-adds stay
+// on the FP64 pipe.  Every operation keeps its IEEE result, and the order of
+// operations is Native<double>'s, so the results are bit-identical to it.
+// Measured on GB300 at 128^3 it is no faster: an integer addition takes ~75
+// integer instructions (twice the pipe time of the FP64 instruction it
+// replaces, in a pipe shared with the sweep's address and index work), and
+// with the additions on the integer pipe (FP64-pipe cycles down 30 %) the
+// launch takes 0.87 ms against 0.85 ms on the FP64 pipe alone; the
+// multiplications' rare-case fallback to the FP64 pipe is evaluated
+// unconditionally by the compiler, so bit 1 saves nothing.  It stays as an
+// option (off by default).
+template <int OFF>
+struct Fp64Int : Native<double> {
+    static constexpr int min_blocks = 2;
+    __device__ static __forceinline__ double dadd(double a, double b) {
+        return (OFF & 1) ? i64f::add(a, b) : __dadd_rn(a, b);
+    }
+    __device__ static __forceinline__ double dsub(double a, double b) {
+        return (OFF & 1) ? i64f::sub(a, b) : __dsub_rn(a, b);
+    }
+    __device__ static __forceinline__ double dmul(double a, double b) {
+        return (OFF & 2) ? i64f::mul(a, b) : __dmul_rn(a, b);
+    }
+    __device__ static __forceinline__ Z add(Z a, Z b) { Z r; r.x = dadd(a.x, b.x); r.y = dadd(a.y, b.y); return r; }
+    __device__ static __forceinline__ Z sub(Z a, Z b) { Z r; r.x = dsub(a.x, b.x); r.y = dsub(a.y, b.y); return r; }
+    __device__ static __forceinline__ Z upd_src(Z x, Z t, Z c, Z d, Z s) {
+        Z r;
+        r.x = __fma_rn(t.x, x.x, s.x); r.x = __fma_rn(-t.y, x.y, r.x);
+        r.x = __fma_rn(c.x, d.x, r.x); r.x = __fma_rn(-c.y, d.y, r.x);
+        r.y = __fma_rn(t.x, x.y, s.y); r.y = __fma_rn(t.y, x.x, r.y);
+        r.y = __fma_rn(c.x, d.y, r.y); r.y = __fma_rn(c.y, d.x, r.y);
+        return r;
+    }
+    __device__ static __forceinline__ Z upd(Z x, Z t, Z c, Z d) {
+        Z r;
+        r.x = dmul(t.x, x.x); r.x = __fma_rn(-t.y, x.y, r.x);
+        r.x = __fma_rn(c.x, d.x, r.x); r.x = __fma_rn(-c.y, d.y, r.x);
+        r.y = dmul(t.x, x.y); r.y = __fma_rn(t.y, x.x, r.y);
+        r.y = __fma_rn(c.x, d.y, r.y); r.y = __fma_rn(c.y, d.x, r.y);
+        return r;
+    }
 };
 
 // ------------------------------------------------------------ FP32 pairs ----

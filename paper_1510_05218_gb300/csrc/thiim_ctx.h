@@ -34,6 +34,7 @@ struct thiim_ctx {
     bool have_coeffs, have_fields, have_norm;
     int zchunk;                  // planes per CTA of the sweep
     int temporal;                // iterations per launch: 1, or 2 (temporal blocking, THIIM_C64)
+    unsigned fp64_int_ops;       // THIIM_C128: binary64 operations run on the integer pipe (THIIM_INT_*)
     double *partials;            // 2 doubles per sweep CTA
     size_t partials_cap;         // in CTAs
     double *norms;               // device: |dF|^2, |F|^2 of the last iteration

@@ -29,6 +29,10 @@ namespace thiim {
 #ifndef THIIM_SWEEP_PAIR_TY
 #define THIIM_SWEEP_PAIR_TY 4
 #endif
+// Integer-pipe binary64 operations of a new THIIM_C128 context.
+#ifndef THIIM_FP64_INT_OPS_DEFAULT
+#define THIIM_FP64_INT_OPS_DEFAULT 0u
+#endif
 constexpr int SWEEP_TX = THIIM_SWEEP_TX;
 constexpr int SWEEP_TY = THIIM_SWEEP_TY;
 constexpr int SWEEP_NT = THIIM_SWEEP_NT;
@@ -49,6 +53,9 @@ static_assert(SWEEP_PAIR_TX * SWEEP_PAIR_TY <= 2 * SWEEP_NT, "pair tile too larg
 // Enqueue one fused iteration; grid = (tiles_x * tiles_y, chunks).
 cudaError_t launch_sweep_f64(const SweepArgs &a, dim3 grid, cudaStream_t s);
 cudaError_t launch_sweep_f32(const SweepArgs &a, dim3 grid, cudaStream_t s);
+// The FP64 sweep with additions (offload = 1) or additions and the leading
+// products (offload = 3) on the integer pipe; bit-identical results.
+cudaError_t launch_sweep_f64_int(const SweepArgs &a, dim3 grid, cudaStream_t s, int offload);
 // FP32-pair arithmetic on complex128 data: fields read as complex128
 // (in_pairs = false) or float4 pairs, written likewise; coefficients are
 // float4 pairs (see split_coeffs).

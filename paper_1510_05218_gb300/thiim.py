@@ -19,6 +19,8 @@ THIIM_PERIODIC_X = 1
 THIIM_PERIODIC_Y = 2
 THIIM_PERIODIC_Z = 4
 THIIM_MAX_MATERIALS = 256
+THIIM_INT_ADD = 1
+THIIM_INT_MUL = 2
 
 _HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "thiim.h")
 _lib = None
@@ -56,6 +58,8 @@ def load_library(build_if_missing: bool = False):
                                  ctypes.c_uint, vp]
     lib.thiim_set_stream.argtypes = [vp, vp]
     lib.thiim_set_tuning.argtypes = [vp, ctypes.c_int, ctypes.c_int]
+    lib.thiim_set_fp64_int_ops.argtypes = [vp, ctypes.c_uint]
+    lib.thiim_set_fp64_int_ops.restype = ctypes.c_int
     lib.thiim_set_coeffs.argtypes = [vp, P28]
     lib.thiim_set_fields.argtypes = [vp, P12]
     lib.thiim_iterate.argtypes = [vp, ctypes.c_int]
@@ -156,6 +160,11 @@ def thiim_set_stream(ctx, stream=None):
 
 def thiim_set_tuning(ctx, temporal_block=1, zchunk=0):
     _check("thiim_set_tuning", load_library().thiim_set_tuning(ctx, int(temporal_block), int(zchunk)))
+
+
+def thiim_set_fp64_int_ops(ctx, ops):
+    """Binary64 operations of the THIIM_C128 sweep computed on the integer pipe (bit-identical results)."""
+    _check("thiim_set_fp64_int_ops", load_library().thiim_set_fp64_int_ops(ctx, int(ops)))
 
 
 def thiim_set_coeffs(ctx, coeffs):
