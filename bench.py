@@ -495,6 +495,56 @@ def _variant_adjoint_steady(p, torch, stream, dev, terms, peak):
             "frac_hbm": _sig(cells * terms * alg / (ms / 1e3) / 1e9 / peak, 3)}
 
 
+def _variant_adjoint_checkpointed(p, torch, stream, dev, reps=2):
+    """The inverse-design gradient of the adjoint workload (128^3, texture box,
+    300 iterations, checkpoint every 20): coefficients from Re eps, the
+    checkpointed solve, the absorbed power J and J.backward() (segment
+    recomputation + reverse sweeps + the permittivity chain rule), timed with
+    CUDA events after one warm-up gradient."""
+    from paper_1510_05218_gb300.autograd import Differentiable
+    from workloads import stack_config
+    st = stack_config("adjoint128")
+    eps = st.eps()
+    sig_d = torch.from_numpy(st.omega * eps.imag * st.absorber_mask()).to(dev)
+    args = (st.sigma_pml_e(), st.sigma_pml_h(), st.omega, st.tau, st.k_s, 1.0)
+    n_it, every = 300, 20
+    with torch.cuda.stream(stream):
+        dmod = Differentiable(st.nx, st.ny, st.nz, stream=stream)
+        eps_im = torch.from_numpy(eps.imag.copy()).to(dev)
+        base = torch.from_numpy(eps.real.copy()).to(dev)
+
+        def grad_once(evs=None):
+            er = base.clone().requires_grad_(True)
+            co = dmod.build_coeffs(er, eps_im, *args)
+            x = dmod.solve(co, n_it, every)
+            ex, ey, ez = x[6] + x[7], x[8] + x[9], x[10] + x[11]
+            J = 0.5 * torch.sum(sig_d * (ex.abs() ** 2 + ey.abs() ** 2 + ez.abs() ** 2))
+            if evs:
+                evs[1].record(stream)
+            J.backward()
+            return er.grad
+
+        try:
+            grad_once()
+            torch.cuda.synchronize()
+            fwd, tot = [], []
+            for _ in range(reps):
+                evs = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+                evs[0].record(stream)
+                grad_once(evs)
+                evs[2].record(stream)
+                torch.cuda.synchronize()
+                fwd.append(evs[0].elapsed_time(evs[1]))
+                tot.append(evs[0].elapsed_time(evs[2]))
+        finally:
+            dmod.close()
+    torch.cuda.empty_cache()
+    cells = st.nx * st.ny * st.nz
+    ms_f, ms_t = min(fwd), min(tot)
+    return {"ms_forward": _sig(ms_f), "ms_backward": _sig(ms_t - ms_f), "gradients_per_s": _sig(1e3 / ms_t, 3),
+            "value": _sig(cells * n_it / (ms_t / 1e3) / 1e6), "dtype": "f64"}
+
+
 def run_grid_sweep(args):
     """MLUP/s against the cubic grid size (64^3 .. 512^3 in steps of 64), one
     JSON line per size and path — the GPU counterpart of the paper's grid-size
@@ -529,6 +579,133 @@ def run_grid_sweep(args):
                               "iters": iters, "zchunk": min(32, n)}), flush=True)
 
 
+def run_extended(args):
+    """Configurations too long for the default run, one JSON line each:
+    C2 — the 128^3 stack converged by native FP64 and by the mixed solver
+    (complex64 corrections, FP64 defect every 50), relative L2 error of each
+    full component of the mixed solution against the FP64 one; C3 — the
+    32-solve batch (FP32-pair arithmetic on complex128 data, 1e-12 oracle
+    parity) run toward relative residual 1e-8 with a bounded iteration count,
+    each solve's residual recorded per chunk so that the iterations a solve
+    still needs can be extrapolated from its asymptotic rate."""
+    import math
+
+    import torch
+
+    import paper_1510_05218_gb300 as p
+    from workloads import batch_configs, stack_config
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    p.load_library()
+    stream = torch.cuda.Stream(device=dev)
+    which = args.extended_configs.split(",")
+
+    if "c2" in which:
+        st = stack_config(args.c2_workload)
+        shape = (st.nz, st.ny, st.nx)
+        cells = st.nx * st.ny * st.nz
+        eps = torch.from_numpy(st.eps()).to(dev)
+        bargs = (st.sigma_pml_e(), st.sigma_pml_h(), st.omega, st.tau, st.k_s, 1.0)
+        ctx = p.thiim_create(st.nx, st.ny, st.nz, p.THIIM_C128, 3, stream)
+        co64 = [torch.empty(shape, dtype=torch.complex128, device=dev) for _ in range(28)]
+        f64 = [torch.zeros(shape, dtype=torch.complex128, device=dev) for _ in range(12)]
+        traj64 = []
+        try:
+            with torch.cuda.stream(stream):
+                p.thiim_build_coeffs(ctx, eps, *bargs, co64)
+            p.thiim_set_coeffs(ctx, co64)
+            p.thiim_set_fields(ctx, f64)
+            it64, r64, t0 = 0, 1.0, time.perf_counter()
+            while it64 < args.c2_max_fp64 and r64 > args.c2_tol_fp64:
+                p.thiim_iterate(ctx, 5000)
+                it64 += 5000
+                r64 = p.thiim_residual(ctx)
+                traj64.append([it64, _sig(r64, 3)])
+            sec64 = time.perf_counter() - t0
+        finally:
+            p.thiim_destroy(ctx)
+        ctx = p.thiim_create(st.nx, st.ny, st.nz, p.THIIM_C64, 3, stream)
+        co32 = [torch.empty(shape, dtype=torch.complex64, device=dev) for _ in range(28)]
+        work = [torch.zeros(shape, dtype=torch.complex64, device=dev) for _ in range(12)]
+        x64 = [torch.zeros(shape, dtype=torch.complex128, device=dev) for _ in range(12)]
+        trajm = []
+        try:
+            with torch.cuda.stream(stream):
+                p.thiim_build_coeffs(ctx, eps, *bargs, co32)
+            p.thiim_set_coeffs(ctx, co32)
+            p.thiim_set_fields(ctx, work)
+            outer, rm, t0, best, stall = 0, 1.0, time.perf_counter(), 1.0, 0
+            while outer < args.c2_max_outer and rm > args.c2_tol_fp64:
+                done, rm = p.thiim_mixed_solve(ctx, co64, x64, args.c2_inner, 500, args.c2_tol_fp64)
+                outer += done
+                trajm.append([outer, _sig(rm, 3)])
+                stall = stall + 1 if rm > 0.9 * best else 0     # floor reached: 2500 outer steps without 10 %
+                best = min(best, rm)
+                if done < 500 or stall >= 5:
+                    break
+            secm = time.perf_counter() - t0
+        finally:
+            p.thiim_destroy(ctx)
+        torch.cuda.synchronize()
+        names = ["Hx", "Hy", "Hz", "Ex", "Ey", "Ez"]
+        errs = {}
+        for c in range(6):
+            ref = f64[2 * c] + f64[2 * c + 1]
+            mix = x64[2 * c] + x64[2 * c + 1]
+            errs[names[c]] = _sig(float(torch.linalg.vector_norm(mix - ref) / torch.linalg.vector_norm(ref)), 3)
+        print(json.dumps({"config": "C2", "workload": "%s (%dx%dx%d)" % (args.c2_workload, st.nx, st.ny, st.nz),
+                          "fp64": {"iterations": it64, "residual": _sig(r64, 3), "seconds": _sig(sec64, 3),
+                                   "mlups": _sig(cells * it64 / sec64 / 1e6), "trajectory": traj64[::4]},
+                          "mixed": {"outer_steps": outer, "inner_per_outer": args.c2_inner, "fp64_residual": _sig(rm, 3),
+                                    "seconds": _sig(secm, 3), "trajectory": trajm},
+                          "rel_l2_err_mixed_vs_fp64": errs, "max_err": max(errs.values()), "bound": 1e-6}),
+              flush=True)
+        del co64, f64, co32, work, x64, eps
+        torch.cuda.empty_cache()
+
+    if "c3" in which:
+        stacks = batch_configs(32, seed=1)
+        probs = [_stack_problem(p, torch, st, "pair", stream, dev) for st in stacks]
+        ctxs = [pr[0] for pr in probs]
+        active = list(range(len(ctxs)))
+        its = [0] * len(ctxs)
+        res = [1.0] * len(ctxs)
+        traj = [[] for _ in ctxs]
+        t0 = time.perf_counter()
+        try:
+            done_total = 0
+            while active and done_total < args.c3_max_iters:
+                chunk = min(args.c3_chunk, args.c3_max_iters - done_total)
+                n, r = p.thiim_batch_iterate([ctxs[b] for b in active], chunk, 100, args.c3_tol)
+                for b, nb, rb in zip(active, n, r):
+                    its[b] += nb
+                    res[b] = rb
+                    traj[b].append([its[b], _sig(rb, 3)])
+                active = [b for b in active if res[b] > args.c3_tol]
+                done_total += chunk
+        finally:
+            for c in ctxs:
+                p.thiim_destroy(c)
+        sec = time.perf_counter() - t0
+        rows = []
+        for b, st in enumerate(stacks):
+            row = {"grid": [st.nx, st.ny, st.nz], "lam": _sig(st.lam, 3), "iters": its[b],
+                   "residual": _sig(res[b], 3), "converged": res[b] <= args.c3_tol}
+            tr = traj[b]
+            if not row["converged"] and len(tr) >= 2 and tr[-1][1] > 0 and tr[-2][1] > 0:
+                rate = (math.log10(tr[-2][1]) - math.log10(tr[-1][1])) / (tr[-1][0] - tr[-2][0])
+                row["decades_per_1e4_iters"] = _sig(rate * 1e4, 3)
+                if rate > 0:
+                    row["iters_to_tol_extrapolated"] = int(its[b] + (math.log10(res[b]) - math.log10(args.c3_tol))
+                                                           / rate)
+            rows.append(row)
+        print(json.dumps({"config": "C3", "solves": len(stacks), "tol": args.c3_tol, "dtype": "f32x2",
+                          "max_iters": args.c3_max_iters, "seconds": _sig(sec, 3),
+                          "converged": sum(r["converged"] for r in rows), "per_solve": rows}), flush=True)
+        del probs
+        torch.cuda.empty_cache()
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -556,6 +733,8 @@ def run_ours(args):
     table = args.coeffs == "table"
     ctx, co, fields, eps = _stack_problem(p, torch, st, args.precision, stream, dev, table=table)
     tuning_info = None
+    if args.fp64_int_ops:
+        p.thiim_set_fp64_int_ops(ctx, args.fp64_int_ops)
     if args.temporal != 1 or args.zchunk:
         p.thiim_set_tuning(ctx, args.temporal, args.zchunk)
         tuning_info = {"choice": [args.temporal, args.zchunk], "source": "command line"}
@@ -673,6 +852,7 @@ def run_ours(args):
         variants["batch32"] = _variant_batch(p, torch, bprec, stream, dev, 200, 50, 1)
         variants["spectrum16x2"] = _variant_spectrum(p, torch, bprec, 16, 200)
         variants["adjoint_steady_128"] = _variant_adjoint_steady(p, torch, stream, dev, 200, peak)
+        variants["adjoint_ckpt_128"] = _variant_adjoint_checkpointed(p, torch, stream, dev)
 
     if rank != 0:
         return
@@ -713,8 +893,10 @@ def run_ours(args):
         "variants_legend": ("MLUP/s of the same 512^3 stack in other arithmetic (pair: FP32 pairs on complex128 "
                             "data, 1e-12 oracle parity; c64: complex64), with 2 iterations per launch, with "
                             "material-table coefficients, mixed c64 + FP64 defect (accuracy: 32^3 converged, vs "
-                            "FP64), 32 uneven batched solves, a 16x2 spectrum and the steady adjoint at 128^3; "
-                            "frac_hbm uses the single-iteration algorithmic bytes"),
+                            "FP64), 32 uneven batched solves, a 16x2 spectrum, the steady adjoint at 128^3 and "
+                            "the checkpointed inverse-design gradient (128^3, 300 iterations, checkpoint every "
+                            "20; value = forward LUP / gradient time); frac_hbm uses the single-iteration "
+                            "algorithmic bytes"),
         "variants": variants,
     }
     print(json.dumps(out), flush=True)
@@ -738,6 +920,18 @@ def main():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--grid-sweep", action="store_true", help="MLUP/s vs grid size 64^3..512^3 (not the headline)")
     ap.add_argument("--zchunk", type=int, default=0, help="z planes per CTA (0: library default)")
+    ap.add_argument("--fp64-int-ops", type=int, default=0,
+                    help="complex128: binary64 adds (1) or adds and products (3) on the integer pipe "
+                         "(bit-identical; thiim_set_fp64_int_ops)")
+    ap.add_argument("--extended-configs", default="", help="c2,c3: convergence runs (minutes; not the headline)")
+    ap.add_argument("--c2-workload", default="stack128")
+    ap.add_argument("--c2-tol-fp64", type=float, default=1e-11)
+    ap.add_argument("--c2-max-fp64", type=int, default=700000)
+    ap.add_argument("--c2-max-outer", type=int, default=20000)
+    ap.add_argument("--c2-inner", type=int, default=50, help="complex64 iterations per FP64 defect")
+    ap.add_argument("--c3-tol", type=float, default=1e-8)
+    ap.add_argument("--c3-max-iters", type=int, default=24000)
+    ap.add_argument("--c3-chunk", type=int, default=4000)
     ap.add_argument("--iters", type=int, default=200)
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--e2e-warmup", type=int, default=1)
@@ -752,6 +946,8 @@ def main():
         run_reference(args)
     elif args.grid_sweep:
         run_grid_sweep(args)
+    elif args.extended_configs:
+        run_extended(args)
     else:
         run_ours(args)
 

@@ -37,13 +37,24 @@ namespace {
 
 // Split table (same as include/thiim.h): difference direction, the two
 // splits of the full component read, the curl sign, the source array or -1.
+// A compile-time function: with the split loops unrolled, the directions and
+// signs fold into the code (no FP64 multiplication by +-1, constant index
+// offsets).
 struct Rule { int d, a, b, sign, src; };
-__constant__ Rule c_rules[12] = {
-    {2, EYX, EYZ, +1, SRC_HXY}, {1, EZX, EZY, -1, -1}, {2, EXY, EXZ, -1, SRC_HYX},
-    {0, EZX, EZY, +1, -1},      {1, EXY, EXZ, +1, -1}, {0, EYX, EYZ, -1, -1},
-    {2, HYX, HYZ, -1, SRC_EXY}, {1, HZX, HZY, +1, -1}, {2, HXY, HXZ, +1, SRC_EYX},
-    {0, HZX, HZY, -1, -1},      {1, HXY, HXZ, -1, -1}, {0, HYX, HYZ, +1, -1},
-};
+__host__ __device__ constexpr Rule rule_of(int s) {
+    return s == HXY ? Rule{2, EYX, EYZ, +1, SRC_HXY}
+         : s == HXZ ? Rule{1, EZX, EZY, -1, -1}
+         : s == HYX ? Rule{2, EXY, EXZ, -1, SRC_HYX}
+         : s == HYZ ? Rule{0, EZX, EZY, +1, -1}
+         : s == HZX ? Rule{1, EXY, EXZ, +1, -1}
+         : s == HZY ? Rule{0, EYX, EYZ, -1, -1}
+         : s == EXY ? Rule{2, HYX, HYZ, -1, SRC_EXY}
+         : s == EXZ ? Rule{1, HZX, HZY, +1, -1}
+         : s == EYX ? Rule{2, HXY, HXZ, +1, SRC_EYX}
+         : s == EYZ ? Rule{0, HZX, HZY, -1, -1}
+         : s == EZX ? Rule{1, HXY, HXZ, -1, -1}
+         :            Rule{0, HYX, HYZ, +1, -1};
+}
 
 struct AdjArgs {
     double2 *lam[12];        // in: adjoint of x^{n+1}; out: adjoint of x^n
@@ -61,20 +72,59 @@ __device__ __forceinline__ double2 c2(double x, double y) { return make_double2(
 __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return c2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ double2 csub(double2 a, double2 b) { return c2(a.x - b.x, a.y - b.y); }
 __device__ __forceinline__ double2 cscale(double s, double2 a) { return c2(s * a.x, s * a.y); }
+// sign * a for a compile-time sign of +-1 (a negation, no multiplication)
+template <int SIGN>
+__device__ __forceinline__ double2 csign(double2 a) { return SIGN > 0 ? a : c2(-a.x, -a.y); }
 __device__ __forceinline__ double2 conjmul(double2 a, double2 b) {   // conj(a) * b
     return c2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
 }
 
-// Linear index of (i, j, k) shifted by +-1 along d, or -1 outside a non-periodic edge.
-__device__ __forceinline__ long long shifted(int i, int j, int k, int d, int off, const AdjArgs &a) {
+// Linear index of (i, j, k) shifted by OFF = +-1 along D, or -1 outside a
+// non-periodic edge.
+template <int D, int OFF>
+__device__ __forceinline__ long long shifted(int i, int j, int k, const AdjArgs &a) {
     int q[3] = {i, j, k};
     const int n[3] = {a.nx, a.ny, a.nz};
-    q[d] += off;
-    if (q[d] < 0 || q[d] >= n[d]) {
-        if (!(a.bc & (1u << d))) return -1;
-        q[d] = (q[d] + n[d]) % n[d];
+    q[D] += OFF;
+    if (q[D] < 0 || q[D] >= n[D]) {
+        if (!(a.bc & (1u << D))) return -1;
+        q[D] = OFF < 0 ? q[D] + n[D] : q[D] - n[D];
     }
     return ((long long)q[2] * a.ny + q[1]) * a.nx + q[0];
+}
+
+// Contribution of E split E to the H components' adjoint: -sign_e D^-_{d(e)} (conj(c_e) mu_e).
+template <int E>
+__device__ __forceinline__ void adj_h_term(const AdjArgs &a, size_t p, int i, int j, int k, double2 A[3]) {
+    constexpr Rule r = rule_of(E);
+    constexpr int comp = r.a / 2;   // H component read (0 = x, 1 = y, 2 = z)
+    const long long q = shifted<r.d, -1>(i, j, k, a);
+    const double2 w0 = conjmul(a.co[C0 + E][p], a.lam[E][p]);
+    const double2 w1 = q < 0 ? c2(0, 0) : conjmul(a.co[C0 + E][q], a.lam[E][q]);
+    A[comp] = cadd(A[comp], csign<-r.sign>(csub(w0, w1)));
+}
+
+template <bool GRAD, int H>
+__device__ __forceinline__ void adj_h_split(const AdjArgs &a, size_t p, int i, int j, int k, const double2 A[3]) {
+    constexpr Rule r = rule_of(H);
+    const double2 lh = cadd(a.lam[H][p], A[H / 2]);
+    if (GRAD) {
+        // D^- of the full E component this split reads, from x^n
+        const long long q = shifted<r.d, -1>(i, j, k, a);
+        const double2 f0 = cadd(a.xn[r.a][p], a.xn[r.b][p]);
+        const double2 f1 = q < 0 ? c2(0, 0) : cadd(a.xn[r.a][q], a.xn[r.b][q]);
+        const double2 dm = csign<r.sign>(csub(f0, f1));
+        // g += lh * conj(v)  ==  conj(conj(lh) * v)
+        const double2 gt = conjmul(a.xn[H][p], lh);
+        const double2 gc = conjmul(dm, lh);
+        a.grad[T0 + H][p] = cadd(a.grad[T0 + H][p], gt);
+        a.grad[C0 + H][p] = cadd(a.grad[C0 + H][p], gc);
+        if (r.src >= 0) a.grad[r.src][p] = cadd(a.grad[r.src][p], lh);
+    }
+    a.lh[H][p] = lh;
+    const double2 nl = conjmul(a.co[T0 + H][p], lh);
+    a.lam[H][p] = nl;
+    if (a.acc[0]) a.acc[H][p] = cadd(a.acc[H][p], nl);
 }
 
 // GRAD = false: propagate lam only (no coefficient gradients, x not read).
@@ -85,36 +135,48 @@ __global__ void adjoint_h_kernel(const AdjArgs a) {
         const int i = (int)(p % a.nx), j = (int)((p / a.nx) % a.ny), k = (int)(p / ((size_t)a.nx * a.ny));
         // A_comp for the three H components: contributions of the E splits reading them
         double2 A[3] = {c2(0, 0), c2(0, 0), c2(0, 0)};
-        for (int e = 6; e < 12; ++e) {
-            const Rule r = c_rules[e];
-            const int comp = r.a / 2;   // H component read (0 = x, 1 = y, 2 = z)
-            const long long q = shifted(i, j, k, r.d, -1, a);
-            const double2 w0 = conjmul(a.co[C0 + e][p], a.lam[e][p]);
-            const double2 w1 = q < 0 ? c2(0, 0) : conjmul(a.co[C0 + e][q], a.lam[e][q]);
-            A[comp] = cadd(A[comp], cscale(-(double)r.sign, csub(w0, w1)));
-        }
-        for (int h = 0; h < 6; ++h) {
-            const Rule r = c_rules[h];
-            const double2 lh = cadd(a.lam[h][p], A[h / 2]);
-            if (GRAD) {
-                // D^- of the full E component this split reads, from x^n
-                const long long q = shifted(i, j, k, r.d, -1, a);
-                const double2 f0 = cadd(a.xn[r.a][p], a.xn[r.b][p]);
-                const double2 f1 = q < 0 ? c2(0, 0) : cadd(a.xn[r.a][q], a.xn[r.b][q]);
-                const double2 dm = cscale((double)r.sign, csub(f0, f1));
-                // g += lh * conj(v)  ==  conj(conj(lh) * v)
-                const double2 gt = conjmul(a.xn[h][p], lh);
-                const double2 gc = conjmul(dm, lh);
-                a.grad[T0 + h][p] = cadd(a.grad[T0 + h][p], gt);
-                a.grad[C0 + h][p] = cadd(a.grad[C0 + h][p], gc);
-                if (r.src >= 0) a.grad[r.src][p] = cadd(a.grad[r.src][p], lh);
-            }
-            a.lh[h][p] = lh;
-            const double2 nl = conjmul(a.co[T0 + h][p], lh);
-            a.lam[h][p] = nl;
-            if (a.acc[0]) a.acc[h][p] = cadd(a.acc[h][p], nl);
-        }
+        adj_h_term<EXY>(a, p, i, j, k, A);
+        adj_h_term<EXZ>(a, p, i, j, k, A);
+        adj_h_term<EYX>(a, p, i, j, k, A);
+        adj_h_term<EYZ>(a, p, i, j, k, A);
+        adj_h_term<EZX>(a, p, i, j, k, A);
+        adj_h_term<EZY>(a, p, i, j, k, A);
+        adj_h_split<GRAD, HXY>(a, p, i, j, k, A);
+        adj_h_split<GRAD, HXZ>(a, p, i, j, k, A);
+        adj_h_split<GRAD, HYX>(a, p, i, j, k, A);
+        adj_h_split<GRAD, HYZ>(a, p, i, j, k, A);
+        adj_h_split<GRAD, HZX>(a, p, i, j, k, A);
+        adj_h_split<GRAD, HZY>(a, p, i, j, k, A);
     }
+}
+
+// Contribution of H split H to the E components' adjoint: -sign_h D^+_{d(h)} (conj(c_h) lh_h).
+template <int H>
+__device__ __forceinline__ void adj_e_term(const AdjArgs &a, size_t p, int i, int j, int k, double2 B[3]) {
+    constexpr Rule r = rule_of(H);
+    constexpr int comp = (r.a - 6) / 2;   // E component read
+    const long long q = shifted<r.d, +1>(i, j, k, a);
+    const double2 v0 = conjmul(a.co[C0 + H][p], a.lh[H][p]);
+    const double2 v1 = q < 0 ? c2(0, 0) : conjmul(a.co[C0 + H][q], a.lh[H][q]);
+    B[comp] = cadd(B[comp], csign<-r.sign>(csub(v1, v0)));
+}
+
+template <bool GRAD, int E>
+__device__ __forceinline__ void adj_e_split(const AdjArgs &a, size_t p, int i, int j, int k, const double2 B[3]) {
+    constexpr Rule r = rule_of(E);
+    const double2 mu = a.lam[E][p];
+    if (GRAD) {
+        const long long q = shifted<r.d, +1>(i, j, k, a);
+        const double2 f0 = cadd(a.xn1[r.a][p], a.xn1[r.b][p]);
+        const double2 f1 = q < 0 ? c2(0, 0) : cadd(a.xn1[r.a][q], a.xn1[r.b][q]);
+        const double2 dp = csign<r.sign>(csub(f1, f0));
+        a.grad[T0 + E][p] = cadd(a.grad[T0 + E][p], conjmul(a.xn[E][p], mu));
+        a.grad[C0 + E][p] = cadd(a.grad[C0 + E][p], conjmul(dp, mu));
+        if (r.src >= 0) a.grad[r.src][p] = cadd(a.grad[r.src][p], mu);
+    }
+    const double2 nl = cadd(conjmul(a.co[T0 + E][p], mu), B[(E - 6) / 2]);
+    a.lam[E][p] = nl;
+    if (a.acc[0]) a.acc[E][p] = cadd(a.acc[E][p], nl);
 }
 
 template <bool GRAD>
@@ -124,30 +186,18 @@ __global__ void adjoint_e_kernel(const AdjArgs a) {
         const int i = (int)(p % a.nx), j = (int)((p / a.nx) % a.ny), k = (int)(p / ((size_t)a.nx * a.ny));
         // B_comp for the three E components: contributions of the H splits reading them
         double2 B[3] = {c2(0, 0), c2(0, 0), c2(0, 0)};
-        for (int h = 0; h < 6; ++h) {
-            const Rule r = c_rules[h];
-            const int comp = (r.a - 6) / 2;   // E component read
-            const long long q = shifted(i, j, k, r.d, +1, a);
-            const double2 v0 = conjmul(a.co[C0 + h][p], a.lh[h][p]);
-            const double2 v1 = q < 0 ? c2(0, 0) : conjmul(a.co[C0 + h][q], a.lh[h][q]);
-            B[comp] = cadd(B[comp], cscale(-(double)r.sign, csub(v1, v0)));
-        }
-        for (int e = 6; e < 12; ++e) {
-            const Rule r = c_rules[e];
-            const double2 mu = a.lam[e][p];
-            if (GRAD) {
-                const long long q = shifted(i, j, k, r.d, +1, a);
-                const double2 f0 = cadd(a.xn1[r.a][p], a.xn1[r.b][p]);
-                const double2 f1 = q < 0 ? c2(0, 0) : cadd(a.xn1[r.a][q], a.xn1[r.b][q]);
-                const double2 dp = cscale((double)r.sign, csub(f1, f0));
-                a.grad[T0 + e][p] = cadd(a.grad[T0 + e][p], conjmul(a.xn[e][p], mu));
-                a.grad[C0 + e][p] = cadd(a.grad[C0 + e][p], conjmul(dp, mu));
-                if (r.src >= 0) a.grad[r.src][p] = cadd(a.grad[r.src][p], mu);
-            }
-            const double2 nl = cadd(conjmul(a.co[T0 + e][p], mu), B[(e - 6) / 2]);
-            a.lam[e][p] = nl;
-            if (a.acc[0]) a.acc[e][p] = cadd(a.acc[e][p], nl);
-        }
+        adj_e_term<HXY>(a, p, i, j, k, B);
+        adj_e_term<HXZ>(a, p, i, j, k, B);
+        adj_e_term<HYX>(a, p, i, j, k, B);
+        adj_e_term<HYZ>(a, p, i, j, k, B);
+        adj_e_term<HZX>(a, p, i, j, k, B);
+        adj_e_term<HZY>(a, p, i, j, k, B);
+        adj_e_split<GRAD, EXY>(a, p, i, j, k, B);
+        adj_e_split<GRAD, EXZ>(a, p, i, j, k, B);
+        adj_e_split<GRAD, EYX>(a, p, i, j, k, B);
+        adj_e_split<GRAD, EYZ>(a, p, i, j, k, B);
+        adj_e_split<GRAD, EZX>(a, p, i, j, k, B);
+        adj_e_split<GRAD, EZY>(a, p, i, j, k, B);
     }
 }
 
@@ -177,7 +227,7 @@ __global__ void eps_grad_kernel(const EpsGradArgs a) {
         const double eps = a.eps[p].x, sig_mat = a.omega * a.eps[p].y;
         double acc = 0.0;
         for (int e = 6; e < 12; ++e) {
-            const double sg = sig_mat + (c_rules[e].d == 2 ? a.sig_e[k] : 0.0);
+            const double sg = sig_mat + ((e == EXY || e == EYX) ? a.sig_e[k] : 0.0);   // z-difference splits
             double2 dt, dc;
             if (eps > 0.0) {
                 const double den = 1.0 + a.tau * sg / eps;

@@ -22,7 +22,7 @@
 // Per pass the CTA reads x^0 and the coefficients once (the second
 // iteration's coefficients are re-read one or two plane steps later, from
 // L2) and writes x^2 once: DRAM bytes per iteration roughly halve, at the
-// price of ~16 % redundant arithmetic on the halo and 4 barriers per plane.
+// price of ~16 % redundant arithmetic on the halo and 2 barriers per plane.
 #pragma once
 
 #include "thiim_sweep.cuh"
@@ -130,12 +130,20 @@ sweep2_kernel(const SweepArgs a) {
     int bh = 0, be = 0;               // sH1/sH1s[bh] receive plane k; sE1/sE1s[be] receive plane k-1
     int b2 = 0;                       // sH2[b2] receives plane k-1
 
+    // Per plane step two barriers: after A (E^0(k) loaded) and after BC
+    // (H^1(k), E^1(k-1) complete).  B and C share a pass, as do D and E: the
+    // E update of a cell needs the new H of the plane above at the same cell
+    // only, which the same thread has just formed; its other inputs were
+    // written before the last barrier.  The next step's A writes the E^0
+    // buffer of plane k-1, which only B of this step read.
     for (int k = z0 - 1; k <= z1 + 1; ++k) {
         const int kk = zin(k);
+        const int km = zin(k - 1);
         // ---- A: E^0(k) sums
         load_E0(k, b0);
         __syncthreads();
-        // ---- B: H^1(k) on the H^1 region; splits kept on the H^2 region
+        // ---- BC: H^1(k) on the H^1 region (splits kept on the H^2 region);
+        //      E^1(k-1) on the E^1 region (splits kept on the tile)
         for (int w = threadIdx.x; w < c1; w += NT) {
             const int u = w % w1 - 1, v = w / w1 - 1;
             const long long p = cell(u, v, kk);
@@ -154,37 +162,32 @@ sweep2_kernel(const SweepArgs a) {
             sH1[bh][v + 1][u + 1] = f;
             if (u >= 0 && v >= 0 && u <= nix && v <= niy)
                 for (int q = 0; q < 6; ++q) sH1s[bh][q][v][u] = s[q];
-        }
-        __syncthreads();
-        // ---- C: E^1(k-1) on the E^1 region; splits kept on the tile
-        {
-            const int km = zin(k - 1);
-            for (int w = threadIdx.x; w < ce; w += NT) {
-                const int u = w % we - 1, v = w / we - 1;
-                const long long p = cell(u, v, km);
-                Vec3<Z> f;
-                f.x = f.y = f.z = A::zero();
+            // E^1(k-1) at the same cell if it lies in the E^1 region [-1, nix] x [-1, niy]
+            if (u <= nix && v <= niy) {
+                const long long pe = cell(u, v, km);
+                Vec3<Z> g;
+                g.x = g.y = g.z = A::zero();
                 Z out[6];
                 for (int q = 0; q < 6; ++q) out[q] = A::zero();
-                if (p >= 0 && k - 1 >= z0 - 1) {
+                if (pe >= 0 && k - 1 >= z0 - 1) {
                     Z o[6];
-                    for (int q = 0; q < 6; ++q) o[q] = A::ld_field(a.src[EXY + q], p);
-                    // H^1 at k-1 lives in sH1[bh ^ 1], at k in sH1[bh]; beyond a Dirichlet top it is zero
-                    Vec3<Z> hzp = sH1[bh][v + 1][u + 1];
-                    e_update(p, sH1[bh ^ 1][v + 1][u + 1], sH1[bh ^ 1][v + 1][u + 2], sH1[bh ^ 1][v + 2][u + 1], hzp, o,
-                             out);
-                    f.x = A::add(out[0], out[1]);
-                    f.y = A::add(out[2], out[3]);
-                    f.z = A::add(out[4], out[5]);
+                    for (int q = 0; q < 6; ++q) o[q] = A::ld_field(a.src[EXY + q], pe);
+                    // H^1 at k-1 lives in sH1[bh ^ 1]; at k it is f (beyond a Dirichlet top, zero)
+                    e_update(pe, sH1[bh ^ 1][v + 1][u + 1], sH1[bh ^ 1][v + 1][u + 2], sH1[bh ^ 1][v + 2][u + 1], f,
+                             o, out);
+                    g.x = A::add(out[0], out[1]);
+                    g.y = A::add(out[2], out[3]);
+                    g.z = A::add(out[4], out[5]);
                 }
-                sE1[be][v + 1][u + 1] = f;
+                sE1[be][v + 1][u + 1] = g;
                 if (u >= 0 && v >= 0 && u < nix && v < niy)
                     for (int q = 0; q < 6; ++q) sE1s[be][q][v][u] = out[q];
             }
         }
         __syncthreads();
-        // ---- D: H^2(k-1) on the H^2 region (stores the tile part)
-        const int k2 = k - 1;
+        // ---- DE: H^2(k-1) on the H^2 region (stores the tile part), then
+        //      E^2(k-2) at the same cell if it is a tile cell
+        const int k2 = k - 1, k3 = k - 2;
         if (k2 >= z0) {
             const int kk2 = zin(k2);
             for (int w = threadIdx.x; w < c2; w += NT) {
@@ -208,25 +211,19 @@ sweep2_kernel(const SweepArgs a) {
                     }
                 }
                 sH2[b2][v][u] = f;
-            }
-        }
-        __syncthreads();
-        // ---- E: E^2(k-2) on the tile
-        const int k3 = k - 2;
-        if (k3 >= z0 && k3 < z1) {
-            const long long kk3 = zin(k3);
-            for (int w = threadIdx.x; w < ct; w += NT) {
-                const int u = w % nix, v = w / nix;
-                const long long p = cell(u, v, (int)kk3);
-                Z o[6], out[6];
-                for (int q = 0; q < 6; ++q) o[q] = sE1s[be ^ 1][q][v][u];
-                e_update(p, sH2[b2 ^ 1][v][u], sH2[b2 ^ 1][v][u + 1], sH2[b2 ^ 1][v + 1][u], sH2[b2][v][u], o, out);
-                for (int q = 0; q < 6; ++q) A::st_field(a.dst[EXY + q], p, out[q]);
-                if (want_norm) {
-                    const Vec3<Z> f1 = sE1[be ^ 1][v + 1][u + 1];
-                    const Z fx = A::add(out[0], out[1]), fy = A::add(out[2], out[3]), fz = A::add(out[4], out[5]);
-                    A::acc_d3(acc_d, fx, f1.x, fy, f1.y, fz, f1.z);
-                    A::acc_n3(acc_x, fx, fy, fz);
+                if (k3 >= z0 && k3 < z1 && u < nix && v < niy) {
+                    const long long kk3 = zin(k3);
+                    const long long pe = cell(u, v, (int)kk3);
+                    Z o[6], out[6];
+                    for (int q = 0; q < 6; ++q) o[q] = sE1s[be ^ 1][q][v][u];
+                    e_update(pe, sH2[b2 ^ 1][v][u], sH2[b2 ^ 1][v][u + 1], sH2[b2 ^ 1][v + 1][u], f, o, out);
+                    for (int q = 0; q < 6; ++q) A::st_field(a.dst[EXY + q], pe, out[q]);
+                    if (want_norm) {
+                        const Vec3<Z> f1 = sE1[be ^ 1][v + 1][u + 1];
+                        const Z fx = A::add(out[0], out[1]), fy = A::add(out[2], out[3]), fz = A::add(out[4], out[5]);
+                        A::acc_d3(acc_d, fx, f1.x, fy, f1.y, fz, f1.z);
+                        A::acc_n3(acc_x, fx, fy, fz);
+                    }
                 }
             }
         }

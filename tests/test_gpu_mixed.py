@@ -150,3 +150,52 @@ def test_mixed_and_native_converge_to_the_fp64_fixed_point():
         p.thiim_destroy(ctx)
     for comp in range(6):
         assert rel_l2(native[comp], ref[comp]) <= 1e-6, (comp, rel_l2(native[comp], ref[comp]))
+
+
+def test_mixed_converged_64_cube_within_1e6_of_native_fp64():
+    """The 64^3 stack (the largest grid of the layered workload whose iteration
+    converges in reach: native FP64 reaches residual 9e-12 in 250k iterations;
+    the 128^3 stack's iteration has a slowly growing mode, see the benchmark's
+    extended C2 run) converged by native FP64 and by the mixed solver with an
+    FP64 defect every 10 complex64 iterations.  Every full component of the
+    mixed solution lies within 1e-6 (relative L2) of the FP64 one.  Measured:
+    3.2e-7 at the mixed floor 1.3e-8; with a defect every 50 iterations the
+    floor is 6.8e-8 and the error 1.5e-6, over the bound."""
+    import torch
+    p = _lib()
+    st = stack_config("stack64")
+    shape = (st.nz, st.ny, st.nx)
+    eps = torch.from_numpy(st.eps()).to("cuda")
+    bargs = (st.sigma_pml_e(), st.sigma_pml_h(), st.omega, st.tau, st.k_s, 1.0)
+    ctx = p.thiim_create(st.nx, st.ny, st.nz, p.THIIM_C128, 3)
+    co64 = [torch.empty(shape, dtype=torch.complex128, device="cuda") for _ in range(28)]
+    f64 = [torch.zeros(shape, dtype=torch.complex128, device="cuda") for _ in range(12)]
+    try:
+        p.thiim_build_coeffs(ctx, eps, *bargs, co64)
+        p.thiim_set_coeffs(ctx, co64)
+        p.thiim_set_fields(ctx, f64)
+        it, r64 = 0, 1.0
+        while it < 300000 and r64 > 1e-11:
+            p.thiim_iterate(ctx, 5000)
+            it += 5000
+            r64 = p.thiim_residual(ctx)
+    finally:
+        p.thiim_destroy(ctx)
+    assert r64 <= 1e-10, r64
+    ctx = p.thiim_create(st.nx, st.ny, st.nz, p.THIIM_C64, 3)
+    co32 = [torch.empty(shape, dtype=torch.complex64, device="cuda") for _ in range(28)]
+    work = [torch.zeros(shape, dtype=torch.complex64, device="cuda") for _ in range(12)]
+    x64 = [torch.zeros(shape, dtype=torch.complex128, device="cuda") for _ in range(12)]
+    try:
+        p.thiim_build_coeffs(ctx, eps, *bargs, co32)
+        p.thiim_set_coeffs(ctx, co32)
+        p.thiim_set_fields(ctx, work)
+        outer, rm = p.thiim_mixed_solve(ctx, co64, x64, 10, 16000, 2e-8)
+    finally:
+        p.thiim_destroy(ctx)
+    assert rm <= 3e-8, (outer, rm)
+    for c in range(6):
+        ref = f64[2 * c] + f64[2 * c + 1]
+        mix = x64[2 * c] + x64[2 * c + 1]
+        err = float(torch.linalg.vector_norm(mix - ref) / torch.linalg.vector_norm(ref))
+        assert err <= 1e-6, (c, err)
