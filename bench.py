@@ -324,7 +324,7 @@ def _variant_sweep(p, torch, st, precision, stream, dev, iters, warmup, steps, p
     torch.cuda.empty_cache()
     return {"value": _sig(cells * iters * steps / (ms_total / 1e3) / 1e6), "dtype": DTYPE[precision],
             "frac_hbm": _sig(achieved / peak, 3), "launch_ms": _sig(launch_s * 1e3 * temporal),
-            "residual": _sig(res[-1], 3), "tuning": list(choice) if choice else None}
+            "tuning": list(choice) if choice else None}
 
 
 def _variant_mixed(p, torch, st, stream, dev, inner, outer, warmup):
@@ -706,6 +706,38 @@ def run_extended(args):
         torch.cuda.empty_cache()
 
 
+def run_one_variant(args):
+    """One variant of the default run alone (for profiling), one JSON line."""
+    import torch
+
+    import paper_1510_05218_gb300 as p
+    from workloads import stack_config
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    p.load_library()
+    stream = torch.cuda.Stream(device=dev)
+    peak, _ = _peaks()
+    st = stack_config(args.workload)
+    v = args.variant
+    if v in ("pair", "c128", "c64"):
+        r = _variant_sweep(p, torch, st, v, stream, dev, args.iters, 1, 1, peak)
+    elif v == "c64_temporal2":
+        r = _variant_sweep(p, torch, st, "c64", stream, dev, args.iters, 1, 1, peak, temporal=2)
+    elif v in ("pair_table", "c64_table"):
+        r = _variant_sweep(p, torch, st, v.split("_")[0], stream, dev, args.iters, 1, 1, peak, table=True)
+    elif v == "mixed":
+        r = _variant_mixed(p, torch, st, stream, dev, 50, 4, 1)
+    elif v == "batch32":
+        r = _variant_batch(p, torch, "pair", stream, dev, args.iters, 50, 1)
+    elif v == "adjoint_steady_128":
+        r = _variant_adjoint_steady(p, torch, stream, dev, args.iters, peak)
+    elif v == "adjoint_ckpt_128":
+        r = _variant_adjoint_checkpointed(p, torch, stream, dev)
+    else:
+        raise SystemExit("unknown variant %s" % v)
+    print(json.dumps({"variant": v, **r}), flush=True)
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -923,6 +955,7 @@ def main():
     ap.add_argument("--fp64-int-ops", type=int, default=0,
                     help="complex128: binary64 adds (1) or adds and products (3) on the integer pipe "
                          "(bit-identical; thiim_set_fp64_int_ops)")
+    ap.add_argument("--variant", default="", help="run one entry of the variants alone (profiling)")
     ap.add_argument("--extended-configs", default="", help="c2,c3: convergence runs (minutes; not the headline)")
     ap.add_argument("--c2-workload", default="stack128")
     ap.add_argument("--c2-tol-fp64", type=float, default=1e-11)
@@ -948,6 +981,8 @@ def main():
         run_grid_sweep(args)
     elif args.extended_configs:
         run_extended(args)
+    elif args.variant:
+        run_one_variant(args)
     else:
         run_ours(args)
 

@@ -18,8 +18,14 @@ namespace thiim {
 bool aligned(const void *p, size_t a) { return ((uintptr_t)p % a) == 0; }
 
 // Tile shape by precision (matches Tile<A> of the kernels the precision runs).
-int tile_w(const thiim_ctx *c) { return c->precision == THIIM_C128_PAIR ? SWEEP_PAIR_TX : SWEEP_TX; }
-int tile_h(const thiim_ctx *c) { return c->precision == THIIM_C128_PAIR ? SWEEP_PAIR_TY : SWEEP_TY; }
+int tile_w(const thiim_ctx *c) {
+    return c->precision == THIIM_C128_PAIR ? Tile<PairArith<1, 1>>::TX
+         : c->precision == THIIM_C128      ? Tile<Native<double>>::TX : Tile<Native<float>>::TX;
+}
+int tile_h(const thiim_ctx *c) {
+    return c->precision == THIIM_C128_PAIR ? Tile<PairArith<1, 1>>::TY
+         : c->precision == THIIM_C128      ? Tile<Native<double>>::TY : Tile<Native<float>>::TY;
+}
 int tiles_x(const thiim_ctx *c) { return (c->nx + tile_w(c) - 1) / tile_w(c); }
 int tiles_y(const thiim_ctx *c) { return (c->ny + tile_h(c) - 1) / tile_h(c); }
 
@@ -369,7 +375,11 @@ int thiim_iterate(thiim_ctx *c, int n_iters) {
     if ((long long)tx * ty > 0x7FFFFFFFLL || chunks > 65535) return THIIM_ERR_ARG;
     const dim3 grid((unsigned)(tx * ty), (unsigned)chunks);
     const size_t ctas = (size_t)tx * ty * chunks;
-    int st = ensure_partials(c, ctas);
+    // the two-iteration kernel's tiles may be taller
+    const int ty2 = (c->ny + SWEEP2_TY - 1) / SWEEP2_TY;
+    const dim3 grid2((unsigned)(tx * ty2), (unsigned)chunks);
+    const size_t ctas2 = (size_t)tx * ty2 * chunks;
+    int st = ensure_partials(c, ctas > ctas2 ? ctas : ctas2);
     if (st) return st;
     if (!c->norms && cudaMalloc(&c->norms, 2 * sizeof(double)) != cudaSuccess) return THIIM_ERR_NOMEM;
 
@@ -425,6 +435,7 @@ int thiim_iterate(thiim_ctx *c, int n_iters) {
         a.table = pair ? c->pair_table : c->table;
     }
     void **from = c->user, **to = c->alt;
+    size_t last_ctas = ctas;     // CTAs (partials) of the last launch
     for (int it = 0; it < n_iters;) {
         // temporal blocking: two iterations per launch while two remain
         // (array coefficients only; the table variant runs one per launch)
@@ -446,10 +457,11 @@ int thiim_iterate(thiim_ctx *c, int n_iters) {
         else if (c->precision == THIIM_C128)
             e = launch_sweep_f64(a, grid, c->stream);
         else if (step == 2)
-            e = launch_sweep2_f32(a, grid, c->stream);
+            e = launch_sweep2_f32(a, grid2, c->stream);
         else
             e = launch_sweep_f32(a, grid, c->stream);
         if (e != cudaSuccess) return THIIM_ERR_CUDA;
+        last_ctas = step == 2 ? ctas2 : ctas;
         void **tmp = from; from = to; to = tmp;
         it += step;
     }
@@ -460,7 +472,7 @@ int thiim_iterate(thiim_ctx *c, int n_iters) {
                 return THIIM_ERR_CUDA;
         }
     }
-    if (finalize_norms(c->partials, ctas, c->norms, c->stream) != cudaSuccess) return THIIM_ERR_CUDA;
+    if (finalize_norms(c->partials, last_ctas, c->norms, c->stream) != cudaSuccess) return THIIM_ERR_CUDA;
     c->have_norm = true;
     return THIIM_OK;
 }

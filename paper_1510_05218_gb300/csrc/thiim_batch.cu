@@ -25,6 +25,11 @@
 
 using namespace thiim;
 
+// z planes per batch item (every solve).
+#ifndef THIIM_BATCH_ZCHUNK
+#define THIIM_BATCH_ZCHUNK 32
+#endif
+
 namespace {
 
 struct BatchDesc {
@@ -43,7 +48,7 @@ struct BatchList {
 };
 
 template <typename A, int MODE>
-__global__ void __launch_bounds__(SWEEP_NT, A::min_blocks)
+__global__ void __launch_bounds__(SWEEP_NT, Tile<A>::MINB)
 batch_kernel(const BatchList L, int parity, int want_norm) {
     __shared__ SweepArgs sa;
     const int n = *L.n_items;
@@ -203,7 +208,7 @@ extern "C" int thiim_batch_iterate(thiim_ctx *const ctx[], int nb, int max_iters
         d.bc = c->bc;
         d.tiles_x = tiles_x(c);
         d.tiles = d.tiles_x * tiles_y(c);
-        d.zchunk = c->nz < 32 ? c->nz : 32;   // similar item sizes across uneven solves
+        d.zchunk = c->nz < THIIM_BATCH_ZCHUNK ? c->nz : THIIM_BATCH_ZCHUNK;   // similar item sizes across solves
         const int chunks = (c->nz + d.zchunk - 1) / d.zchunk;
         first[b] = total_items;
         count[b] = d.tiles * chunks;

@@ -75,6 +75,17 @@ bool aligned_to(const void *p, size_t a) { return ((size_t)p % a) == 0; }
 
 }  // namespace
 
+namespace thiim {
+
+// The FP64 sweep on 32 x 8 tiles (this entry point's tiling for both
+// precisions; thiim_iterate's FP64 tile is 32 x 16).
+cudaError_t launch_sweep_f64_t8(const SweepArgs &a, dim3 grid, cudaStream_t s) {
+    sweep_kernel<Native<double>, SWEEP_TX, SWEEP_TY, SWEEP_NT, SWEEP_MINB><<<grid, SWEEP_NT, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace thiim
+
 extern "C" int thiim_step_noalloc(int nx, int ny, int nz, int precision, unsigned bc_flags,
                                   void *const src[THIIM_N_FIELDS], void *const dst[THIIM_N_FIELDS],
                                   void *const coeff[THIIM_N_COEFFS], void *cuda_stream,
@@ -128,7 +139,7 @@ extern "C" int thiim_step_noalloc(int nx, int ny, int nz, int precision, unsigne
     a.partials = scratch;   // nullptr: no reduction
     cudaStream_t s = (cudaStream_t)cuda_stream;
     const dim3 grid((unsigned)tiles, (unsigned)chunks);
-    cudaError_t e = precision == THIIM_C128 ? launch_sweep_f64(a, grid, s) : launch_sweep_f32(a, grid, s);
+    cudaError_t e = precision == THIIM_C128 ? launch_sweep_f64_t8(a, grid, s) : launch_sweep_f32(a, grid, s);
     if (e != cudaSuccess) return THIIM_ERR_CUDA;
     if (!rel_residual) return THIIM_OK;
     noalloc_finalize<<<1, 256, 0, s>>>(ctas);

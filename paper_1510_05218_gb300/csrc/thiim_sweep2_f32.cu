@@ -5,7 +5,7 @@
 namespace thiim {
 
 cudaError_t launch_sweep2_f32(const SweepArgs &a, dim3 grid, cudaStream_t s) {
-    sweep2_kernel<Native<float>, SWEEP_TX, SWEEP_TY, 2 * SWEEP_NT><<<grid, 2 * SWEEP_NT, 0, s>>>(a);
+    sweep2_kernel<Native<float>, SWEEP_TX, SWEEP2_TY, SWEEP2_NT><<<grid, SWEEP2_NT, 0, s>>>(a);
     return cudaGetLastError();
 }
 

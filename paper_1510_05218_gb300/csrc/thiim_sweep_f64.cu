@@ -4,7 +4,8 @@
 namespace thiim {
 
 cudaError_t launch_sweep_f64(const SweepArgs &a, dim3 grid, cudaStream_t s) {
-    sweep_kernel<Native<double>, SWEEP_TX, SWEEP_TY, SWEEP_NT, SWEEP_MINB><<<grid, SWEEP_NT, 0, s>>>(a);
+    typedef Tile<Native<double>> T;
+    sweep_kernel<Native<double>, T::TX, T::TY, SWEEP_NT, T::MINB><<<grid, SWEEP_NT, 0, s>>>(a);
     return cudaGetLastError();
 }
 

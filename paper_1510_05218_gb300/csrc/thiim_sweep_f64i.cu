@@ -6,9 +6,11 @@ namespace thiim {
 
 cudaError_t launch_sweep_f64_int(const SweepArgs &a, dim3 grid, cudaStream_t s, int offload) {
     if (offload == 1)
-        sweep_kernel<Fp64Int<1>, SWEEP_TX, SWEEP_TY, SWEEP_NT, SWEEP_MINB><<<grid, SWEEP_NT, 0, s>>>(a);
+        sweep_kernel<Fp64Int<1>, Tile<Fp64Int<1>>::TX, Tile<Fp64Int<1>>::TY, SWEEP_NT, Tile<Fp64Int<1>>::MINB>
+            <<<grid, SWEEP_NT, 0, s>>>(a);
     else if (offload == 3)
-        sweep_kernel<Fp64Int<3>, SWEEP_TX, SWEEP_TY, SWEEP_NT, SWEEP_MINB><<<grid, SWEEP_NT, 0, s>>>(a);
+        sweep_kernel<Fp64Int<3>, Tile<Fp64Int<3>>::TX, Tile<Fp64Int<3>>::TY, SWEEP_NT, Tile<Fp64Int<3>>::MINB>
+            <<<grid, SWEEP_NT, 0, s>>>(a);
     else
         return cudaErrorInvalidValue;
     return cudaGetLastError();

@@ -11,8 +11,8 @@ for the GPU kernels here:
 * ``gpu_footprint`` gives, for a launch configuration (iterations per launch,
   z planes per CTA), the shared memory one CTA needs and the data a launch
   must find again in L2; ``gpu_code_balance`` the DRAM bytes per cell and
-  iteration including the halo the tiles re-read (32 x 8 cells; 64 x 4 for
-  the FP32-pair sweeps).  A candidate is
+  iteration including the halo the tiles re-read (32 x 8 cells for
+  complex64, 32 x 16 for FP64, 64 x 4 for the FP32-pair sweeps).  A candidate is
   admitted if its shared memory fits a CTA, its L2 set stays within half of
   L2 (the paper's "half the cache is usable for tile data" rule, Sec. III-C)
   and its grid fills the resident slots; the library default is always a
@@ -67,8 +67,8 @@ def elem_bytes(precision: int) -> int:
 
 
 def tile(precision: int):
-    """(TX, TY) of the sweep kernels a precision runs."""
-    return (PAIR_TX, PAIR_TY) if precision == 2 else (TX, TY)
+    """(TX, TY) of the sweep kernels a precision runs (FP64: 32 x 16)."""
+    return (PAIR_TX, PAIR_TY) if precision == 2 else ((TX, 2 * TY) if precision == 0 else (TX, TY))
 
 
 def gpu_footprint(precision: int, temporal: int, zchunk: int, ctas: int, n_sm: int, l2_bytes: int):
@@ -90,7 +90,7 @@ def gpu_footprint(precision: int, temporal: int, zchunk: int, ctas: int, n_sm: i
     TX, TY = tile(precision)
     if temporal == 1:
         smem = b * 3 * 2 * ((TX + 2) * (TY + 2) + (TX + 1) * (TY + 1))
-        per_sm = 5 if precision == 1 else (3 if precision == 0 else 2)
+        per_sm = 5 if precision == 1 else 2
         l2_set = 0
     else:
         smem = b * (3 * 2 * ((TX + 4) * (TY + 4) + (TX + 3) * (TY + 3) + (TX + 2) * (TY + 2) + (TX + 1) * (TY + 1))

@@ -158,9 +158,10 @@ def test_mixed_converged_64_cube_within_1e6_of_native_fp64():
     the 128^3 stack's iteration has a slowly growing mode, see the benchmark's
     extended C2 run) converged by native FP64 and by the mixed solver with an
     FP64 defect every 10 complex64 iterations.  Every full component of the
-    mixed solution lies within 1e-6 (relative L2) of the FP64 one.  Measured:
-    3.2e-7 at the mixed floor 1.3e-8; with a defect every 50 iterations the
-    floor is 6.8e-8 and the error 1.5e-6, over the bound."""
+    mixed solution lies within 1e-6 (relative L2) of the FP64 one at the mixed
+    solver's residual floor.  Measured: 3.2e-7 at the floor 1.3e-8 (13500 outer
+    steps); with a defect every 50 iterations the floor is 6.8e-8 and the error
+    1.5e-6, over the bound."""
     import torch
     p = _lib()
     st = stack_config("stack64")
@@ -190,7 +191,15 @@ def test_mixed_converged_64_cube_within_1e6_of_native_fp64():
         p.thiim_build_coeffs(ctx, eps, *bargs, co32)
         p.thiim_set_coeffs(ctx, co32)
         p.thiim_set_fields(ctx, work)
-        outer, rm = p.thiim_mixed_solve(ctx, co64, x64, 10, 16000, 2e-8)
+        # to the mixed solver's floor: chunks of 500 outer steps until five in a
+        # row gain less than 10 % (stopping at residual 2e-8 left 1.3e-6: the
+        # slow tail of the iteration)
+        outer, best, stall, rm = 0, 1.0, 0, 1.0
+        while outer < 20000 and stall < 5:
+            done, rm = p.thiim_mixed_solve(ctx, co64, x64, 10, 500, 0.0)
+            outer += done
+            stall = stall + 1 if rm > 0.9 * best else 0
+            best = min(best, rm)
     finally:
         p.thiim_destroy(ctx)
     assert rm <= 3e-8, (outer, rm)

