@@ -674,7 +674,7 @@ def run_extended(args):
         t0 = time.perf_counter()
         try:
             done_total = 0
-            while active and done_total < args.c3_max_iters:
+            while active and done_total < args.c3_max_iters and time.perf_counter() - t0 < args.c3_max_seconds:
                 chunk = min(args.c3_chunk, args.c3_max_iters - done_total)
                 n, r = p.thiim_batch_iterate([ctxs[b] for b in active], chunk, 100, args.c3_tol)
                 for b, nb, rb in zip(active, n, r):
@@ -700,7 +700,7 @@ def run_extended(args):
                                                            / rate)
             rows.append(row)
         print(json.dumps({"config": "C3", "solves": len(stacks), "tol": args.c3_tol, "dtype": "f32x2",
-                          "max_iters": args.c3_max_iters, "seconds": _sig(sec, 3),
+                          "max_iters": args.c3_max_iters, "max_seconds": args.c3_max_seconds, "seconds": _sig(sec, 3),
                           "converged": sum(r["converged"] for r in rows), "per_solve": rows}), flush=True)
         del probs
         torch.cuda.empty_cache()
@@ -965,6 +965,7 @@ def main():
     ap.add_argument("--c3-tol", type=float, default=1e-8)
     ap.add_argument("--c3-max-iters", type=int, default=24000)
     ap.add_argument("--c3-chunk", type=int, default=4000)
+    ap.add_argument("--c3-max-seconds", type=float, default=1e9, help="stop C3 after this wall time")
     ap.add_argument("--iters", type=int, default=200)
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--e2e-warmup", type=int, default=1)

@@ -86,7 +86,8 @@ enum thiim_status {
  * pipe (thiim_set_fp64_int_ops). */
 enum thiim_int_ops {
     THIIM_INT_ADD = 1u,   /* additions and subtractions */
-    THIIM_INT_MUL = 2u    /* the leading product t * x of the updates without a source */
+    THIIM_INT_MUL = 2u,   /* the leading product t * x of the updates without a source */
+    THIIM_INT_SUMS = 4u   /* only the additions forming the full-field sums (not the differences) */
 };
 
 /* Number of field / coefficient arrays (Sec. III). */
@@ -140,8 +141,8 @@ int thiim_set_tuning(thiim_ctx *ctx, int temporal_block, int zchunk);
  * results; the rest on the FP64 pipe).  The fused multiply-adds always use
  * the FP64 pipe.  Measured on GB300 the sweep is not faster with either (an
  * integer addition costs ~75 integer instructions), so the default is 0.
- *   ops: 0 (everything on the FP64 pipe, the default), THIIM_INT_ADD, or
- *        THIIM_INT_ADD | THIIM_INT_MUL.
+ *   ops: 0 (everything on the FP64 pipe, the default), THIIM_INT_ADD,
+ *        THIIM_INT_ADD | THIIM_INT_MUL, or THIIM_INT_SUMS.
  * Errors: THIIM_ERR_ARG (not a THIIM_C128 context, other values).
  */
 int thiim_set_fp64_int_ops(thiim_ctx *ctx, unsigned ops);

@@ -15,9 +15,15 @@
 // the coefficient gradients (accumulated)
 //   g_t[h] += lh_h conj(H_h^n)   g_c[h] += lh_h conj(sign_h D^-_{d(h)} E^n)   g_Src += lh_h
 //   g_t[e] += mu_e conj(E_e^n)   g_c[e] += mu_e conj(sign_e D^+_{d(e)} H^{n+1/2})   g_Src += mu_e.
-// Kernel R1 computes lh (kept in scratch), lam_H and the H gradients; kernel
-// R2 the new lam_E and the E gradients.  Both are gather kernels, one thread
-// per cell (the adjoint is not the benchmarked path), in FP64.
+// Kernel R1 computes lh, lam_H and the H gradients; kernel R2 the new lam_E
+// and the E gradients.  Both are gather kernels, one thread per cell, in FP64
+// (FP64-pipe bound, like the forward sweep).  The products a difference
+// needs at a cell and at its neighbour are formed once per cell: R1 stores
+// v_h = conj(c_h) lh_h for R2, and R2 stores w_e = conj(c_e) lam_e for the next
+// step's R1 (adjoint_w_kernel forms w from the incoming lam before the first
+// step).  Same operations on the same values as forming them where they are
+// used, so the results are unchanged, with 96 instead of 120 FP64
+// instructions per cell and kernel.
 //
 // Steady state (thiim_adjoint_steady): at a fixed point x* = F(x*) every
 // state of the reverse iteration is x*, so its gradient contributions sum to
@@ -62,7 +68,8 @@ struct AdjArgs {
     const double2 *xn[12];   // x^n (GRAD kernels only)
     const double2 *xn1[12];  // x^{n+1} (GRAD kernels only)
     const double2 *co[28];
-    double2 *lh[6];          // scratch: adjoint of H^{n+1/2}
+    double2 *v[6];           // scratch: conj(c_h) lh_h per H split (lh: adjoint of H^{n+1/2})
+    double2 *w[6];           // scratch: conj(c_e) lam_e per E split, for the next H kernel
     double2 *acc[12];        // if acc[0]: acc += the new lam (steady-state sum)
     int nx, ny, nz;
     unsigned bc;
@@ -93,14 +100,15 @@ __device__ __forceinline__ long long shifted(int i, int j, int k, const AdjArgs 
     return ((long long)q[2] * a.ny + q[1]) * a.nx + q[0];
 }
 
-// Contribution of E split E to the H components' adjoint: -sign_e D^-_{d(e)} (conj(c_e) mu_e).
+// Contribution of E split E to the H components' adjoint: -sign_e D^-_{d(e)} w_e,
+// w_e = conj(c_e) mu_e (formed by the previous E kernel or adjoint_w_kernel).
 template <int E>
 __device__ __forceinline__ void adj_h_term(const AdjArgs &a, size_t p, int i, int j, int k, double2 A[3]) {
     constexpr Rule r = rule_of(E);
     constexpr int comp = r.a / 2;   // H component read (0 = x, 1 = y, 2 = z)
     const long long q = shifted<r.d, -1>(i, j, k, a);
-    const double2 w0 = conjmul(a.co[C0 + E][p], a.lam[E][p]);
-    const double2 w1 = q < 0 ? c2(0, 0) : conjmul(a.co[C0 + E][q], a.lam[E][q]);
+    const double2 w0 = a.w[E - 6][p];
+    const double2 w1 = q < 0 ? c2(0, 0) : a.w[E - 6][q];
     A[comp] = cadd(A[comp], csign<-r.sign>(csub(w0, w1)));
 }
 
@@ -121,7 +129,7 @@ __device__ __forceinline__ void adj_h_split(const AdjArgs &a, size_t p, int i, i
         a.grad[C0 + H][p] = cadd(a.grad[C0 + H][p], gc);
         if (r.src >= 0) a.grad[r.src][p] = cadd(a.grad[r.src][p], lh);
     }
-    a.lh[H][p] = lh;
+    a.v[H][p] = conjmul(a.co[C0 + H][p], lh);
     const double2 nl = conjmul(a.co[T0 + H][p], lh);
     a.lam[H][p] = nl;
     if (a.acc[0]) a.acc[H][p] = cadd(a.acc[H][p], nl);
@@ -150,14 +158,15 @@ __global__ void adjoint_h_kernel(const AdjArgs a) {
     }
 }
 
-// Contribution of H split H to the E components' adjoint: -sign_h D^+_{d(h)} (conj(c_h) lh_h).
+// Contribution of H split H to the E components' adjoint: -sign_h D^+_{d(h)} v_h,
+// v_h = conj(c_h) lh_h (formed by the H kernel).
 template <int H>
 __device__ __forceinline__ void adj_e_term(const AdjArgs &a, size_t p, int i, int j, int k, double2 B[3]) {
     constexpr Rule r = rule_of(H);
     constexpr int comp = (r.a - 6) / 2;   // E component read
     const long long q = shifted<r.d, +1>(i, j, k, a);
-    const double2 v0 = conjmul(a.co[C0 + H][p], a.lh[H][p]);
-    const double2 v1 = q < 0 ? c2(0, 0) : conjmul(a.co[C0 + H][q], a.lh[H][q]);
+    const double2 v0 = a.v[H][p];
+    const double2 v1 = q < 0 ? c2(0, 0) : a.v[H][q];
     B[comp] = cadd(B[comp], csign<-r.sign>(csub(v1, v0)));
 }
 
@@ -176,6 +185,7 @@ __device__ __forceinline__ void adj_e_split(const AdjArgs &a, size_t p, int i, i
     }
     const double2 nl = cadd(conjmul(a.co[T0 + E][p], mu), B[(E - 6) / 2]);
     a.lam[E][p] = nl;
+    a.w[E - 6][p] = conjmul(a.co[C0 + E][p], nl);
     if (a.acc[0]) a.acc[E][p] = cadd(a.acc[E][p], nl);
 }
 
@@ -199,6 +209,13 @@ __global__ void adjoint_e_kernel(const AdjArgs a) {
         adj_e_split<GRAD, EZX>(a, p, i, j, k, B);
         adj_e_split<GRAD, EZY>(a, p, i, j, k, B);
     }
+}
+
+// w_e = conj(c_e) lam_e for the six E splits: the first H kernel's input.
+__global__ void adjoint_w_kernel(const AdjArgs a) {
+    const size_t n = (size_t)a.nx * a.ny * a.nz;
+    for (size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (size_t)gridDim.x * blockDim.x)
+        for (int e = 0; e < 6; ++e) a.w[e][p] = conjmul(a.co[C0 + EXY + e][p], a.lam[EXY + e][p]);
 }
 
 // ---- d J / d Re(eps) from the coefficient gradients (chain rule of Eqs. 3-5) ----
@@ -254,6 +271,10 @@ int ensure_adjoint_scratch(thiim_ctx *c, int n_back) {
     if (!c->adj_lh[0]) {
         for (int i = 0; i < 6; ++i)
             if (cudaMalloc(&c->adj_lh[i], c->n_cells * 16) != cudaSuccess) { cudaGetLastError(); return THIIM_ERR_NOMEM; }
+    }
+    if (!c->adj_w[0]) {
+        for (int i = 0; i < 6; ++i)
+            if (cudaMalloc(&c->adj_w[i], c->n_cells * 16) != cudaSuccess) { cudaGetLastError(); return THIIM_ERR_NOMEM; }
     }
     if (c->adj_cap < n_back) {
         for (int m = 0; m < c->adj_cap; ++m)
@@ -314,11 +335,15 @@ extern "C" int thiim_adjoint_iterate(thiim_ctx *c, void *const lambda[THIIM_N_FI
         a.grad[i] = (double2 *)grad_coeff[i];
         a.co[i] = (const double2 *)c->coeff[i];
     }
-    for (int i = 0; i < 6; ++i) a.lh[i] = (double2 *)c->adj_lh[i];
+    for (int i = 0; i < 6; ++i) {
+        a.v[i] = (double2 *)c->adj_lh[i];
+        a.w[i] = (double2 *)c->adj_w[i];
+    }
     a.nx = c->nx; a.ny = c->ny; a.nz = c->nz;
     a.bc = c->bc;
     size_t blocks = (c->n_cells + 255) / 256;
     if (blocks > 8u * (size_t)c->num_sms) blocks = 8u * (size_t)c->num_sms;
+    adjoint_w_kernel<<<(unsigned)blocks, 256, 0, c->stream>>>(a);
     for (int m = n_back - 1; m >= 0; --m) {
         for (int i = 0; i < THIIM_N_FIELDS; ++i) {
             a.xn[i] = (const double2 *)(m == 0 ? fwd_checkpoint[i] : c->adj_states[m - 1][i]);
@@ -417,11 +442,15 @@ extern "C" int thiim_adjoint_steady(thiim_ctx *c, void *const lambda[THIIM_N_FIE
         a.acc[i] = (double2 *)lambda[i];          // lam* so far (starts as g)
     }
     for (int i = 0; i < THIIM_N_COEFFS; ++i) a.co[i] = (const double2 *)c->coeff[i];
-    for (int i = 0; i < 6; ++i) a.lh[i] = (double2 *)c->adj_lh[i];
+    for (int i = 0; i < 6; ++i) {
+        a.v[i] = (double2 *)c->adj_lh[i];
+        a.w[i] = (double2 *)c->adj_w[i];
+    }
     a.nx = c->nx; a.ny = c->ny; a.nz = c->nz;
     a.bc = c->bc;
     size_t blocks = (c->n_cells + 255) / 256;
     if (blocks > 8u * (size_t)c->num_sms) blocks = 8u * (size_t)c->num_sms;
+    adjoint_w_kernel<<<(unsigned)blocks, 256, 0, c->stream>>>(a);
     int k = 1;
     double rel = 1.0;
     bool have_rel = false;
@@ -452,6 +481,7 @@ extern "C" int thiim_adjoint_steady(thiim_ctx *c, void *const lambda[THIIM_N_FIE
         a.xn1[i] = (const double2 *)x_star[i];
     }
     for (int i = 0; i < THIIM_N_COEFFS; ++i) a.grad[i] = (double2 *)grad_coeff[i];
+    adjoint_w_kernel<<<(unsigned)blocks, 256, 0, c->stream>>>(a);
     adjoint_h_kernel<true><<<(unsigned)blocks, 256, 0, c->stream>>>(a);
     adjoint_e_kernel<true><<<(unsigned)blocks, 256, 0, c->stream>>>(a);
     if (cudaGetLastError() != cudaSuccess) return THIIM_ERR_CUDA;

@@ -307,7 +307,8 @@ int thiim_set_tuning(thiim_ctx *c, int temporal_block, int zchunk) {
 
 int thiim_set_fp64_int_ops(thiim_ctx *c, unsigned ops) {
     if (!c || c->precision != THIIM_C128) return THIIM_ERR_ARG;
-    if (ops != 0u && ops != THIIM_INT_ADD && ops != (THIIM_INT_ADD | THIIM_INT_MUL)) return THIIM_ERR_ARG;
+    if (ops != 0u && ops != THIIM_INT_ADD && ops != (THIIM_INT_ADD | THIIM_INT_MUL) && ops != THIIM_INT_SUMS)
+        return THIIM_ERR_ARG;
     c->fp64_int_ops = ops;
     return THIIM_OK;
 }
@@ -563,8 +564,10 @@ void thiim_destroy(thiim_ctx *c) {
         if (c->pair_co[i]) cudaFree(c->pair_co[i]);
     for (int i = 0; i < THIIM_N_FIELDS; ++i)
         if (c->mix_r[i]) cudaFree(c->mix_r[i]);
-    for (int i = 0; i < 6; ++i)
+    for (int i = 0; i < 6; ++i) {
         if (c->adj_lh[i]) cudaFree(c->adj_lh[i]);
+        if (c->adj_w[i]) cudaFree(c->adj_w[i]);
+    }
     for (int m = 0; m < THIIM_MAX_ADJOINT_SEGMENT; ++m)
         for (int i = 0; i < THIIM_N_FIELDS; ++i)
             if (c->adj_states[m][i]) cudaFree(c->adj_states[m][i]);

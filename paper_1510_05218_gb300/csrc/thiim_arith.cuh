@@ -127,8 +127,9 @@ struct Native {
 // without a source term).  GB300's FP64 pipe retires ~1.7 of them per SM and
 // clock, its integer units 64-128.  OFF selects which operations run as
 // integer-pipe binary64 arithmetic instead (thiim_i64f.cuh; bit 0: additions
-// and subtractions, bit 1: the leading products); the fused multiply-adds stay
-// on the FP64 pipe.  Every operation keeps its IEEE result, and the order of
+// and subtractions, bit 2: the additions of the full-field sums only (A::add,
+// not the differences A::sub), bit 1: the leading products); the fused
+// multiply-adds stay on the FP64 pipe.  Every operation keeps its IEEE result, and the order of
 // operations is Native<double>'s, so the results are bit-identical to it.
 // Measured on GB300 at 128^3 it is no faster: an integer addition takes ~75
 // integer instructions (twice the pipe time of the FP64 instruction it
@@ -142,7 +143,7 @@ template <int OFF>
 struct Fp64Int : Native<double> {
     static constexpr int min_blocks = 2;
     __device__ static __forceinline__ double dadd(double a, double b) {
-        return (OFF & 1) ? i64f::add(a, b) : __dadd_rn(a, b);
+        return (OFF & 5) ? i64f::add(a, b) : __dadd_rn(a, b);
     }
     __device__ static __forceinline__ double dsub(double a, double b) {
         return (OFF & 1) ? i64f::sub(a, b) : __dsub_rn(a, b);

@@ -44,7 +44,8 @@ struct thiim_ctx {
     // defect-correction state (thiim_mixed_solve)
     void *mix_r[THIIM_N_FIELDS]; // complex64 defect r = F64(x) - x
     // adjoint state (thiim_adjoint_iterate)
-    void *adj_lh[6];             // adjoint of H^{n+1/2}
+    void *adj_lh[6];             // conj(c_h) times the adjoint of H^{n+1/2}, per H split
+    void *adj_w[6];              // conj(c_e) times the adjoint of E, per E split
     void *adj_states[THIIM_MAX_ADJOINT_SEGMENT][THIIM_N_FIELDS];  // recomputed iterates
     int adj_cap;                 // complete recomputed-iterate sets allocated
     double *adj_norms;           // device: 2 doubles, thiim_adjoint_steady's convergence check

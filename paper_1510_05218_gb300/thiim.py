@@ -21,6 +21,7 @@ THIIM_PERIODIC_Z = 4
 THIIM_MAX_MATERIALS = 256
 THIIM_INT_ADD = 1
 THIIM_INT_MUL = 2
+THIIM_INT_SUMS = 4
 
 _HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "thiim.h")
 _lib = None

@@ -19,7 +19,7 @@ from workloads import random_coeffs, random_fields
 pytestmark = pytest.mark.gpu
 
 SHAPES = [(9, 13, 70), (5, 17, 33), (40, 9, 31), (1, 5, 7)]
-MODES = [0, 1, 3]
+MODES = [0, 1, 3, 4]
 
 
 def _lib():
@@ -91,7 +91,7 @@ def test_integer_pipe_modes_are_bit_identical(shape, bc, salted):
         f, c = _salt(f, 1), _salt(c, 2)
     runs = {ops: _run(p, f, c, 3, bc, ops) for ops in MODES}
     ref_bits, ref_r, _ = runs[0]
-    for ops in (1, 3):
+    for ops in (1, 3, 4):
         bits, r, _ = runs[ops]
         assert r == ref_r or (np.isnan(r) and np.isnan(ref_r))
         for s in range(12):
@@ -121,10 +121,18 @@ def test_set_fp64_int_ops_arguments():
         p.thiim_destroy(ctx)
     ctx = p.thiim_create(8, 8, 8, p.THIIM_C128, 3)
     try:
-        for bad in (2, 4, 7):
+        for bad in (2, 5, 7):
             with pytest.raises(p.ThiimError):
                 p.thiim_set_fp64_int_ops(ctx, bad)
-        for good in (0, 1, 3):
+        for good in (0, 1, 3, 4):
             p.thiim_set_fp64_int_ops(ctx, good)
     finally:
         p.thiim_destroy(ctx)
+
+
+def test_fp64_pipe_rate_is_plausible():
+    """thiim_fp64_pipe_rate (the FP64 roofline's denominator) reports a device-wide
+    FMA rate between 1/4 and 4x of GB300's 152 SMs x 2 FMA/clk x ~2 GHz."""
+    p = _lib()
+    r = p.thiim_fp64_pipe_rate()
+    assert 1.5e11 <= r <= 2.5e12, r
