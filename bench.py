@@ -663,6 +663,61 @@ def run_extended(args):
         del co64, f64, co32, work, x64, eps
         torch.cuda.empty_cache()
 
+    if "diverge" in which:
+        # where the last update of a non-converging stack lives: per z plane, per
+        # material and per full component, after --diverge-iters FP64 iterations
+        st = stack_config(args.c2_workload)
+        shape = (st.nz, st.ny, st.nx)
+        eps = torch.from_numpy(st.eps()).to(dev)
+        ctx = p.thiim_create(st.nx, st.ny, st.nz, p.THIIM_C128, 3, stream)
+        co = [torch.empty(shape, dtype=torch.complex128, device=dev) for _ in range(28)]
+        f = [torch.zeros(shape, dtype=torch.complex128, device=dev) for _ in range(12)]
+        try:
+            with torch.cuda.stream(stream):
+                p.thiim_build_coeffs(ctx, eps, st.sigma_pml_e(), st.sigma_pml_h(), st.omega, st.tau, st.k_s, 1.0, co)
+            p.thiim_set_coeffs(ctx, co)
+            p.thiim_set_fields(ctx, f)
+            done = 0
+            while done < args.diverge_iters:
+                n = min(10000, args.diverge_iters - done)
+                p.thiim_iterate(ctx, n)
+                done += n
+            r0 = p.thiim_residual(ctx)
+            torch.cuda.synchronize()
+            prev = [t.clone() for t in f]
+            p.thiim_iterate(ctx, 1)
+            r1 = p.thiim_residual(ctx)
+            torch.cuda.synchronize()
+        finally:
+            p.thiim_destroy(ctx)
+        names = ["Hx", "Hy", "Hz", "Ex", "Ey", "Ez"]
+        d2 = [((f[2 * c] + f[2 * c + 1]) - (prev[2 * c] + prev[2 * c + 1])).abs() ** 2 for c in range(6)]
+        x2 = [(f[2 * c] + f[2 * c + 1]).abs() ** 2 for c in range(6)]
+        dtot = sum(float(t.sum()) for t in d2)
+        xtot = sum(float(t.sum()) for t in x2)
+        dplane = sum(t.sum(dim=(1, 2)) for t in d2).cpu().numpy() / dtot
+        xplane = sum(t.sum(dim=(1, 2)) for t in x2).cpu().numpy() / xtot
+        ids = torch.from_numpy(st.material_ids()).to(dev)
+        dsum = sum(d2)
+        mat = {st.MATERIAL_ORDER[m]: _sig(float(dsum[ids == m].sum()) / dtot, 3) for m in range(4)}
+        # split differences (Hxy - Hxz, ...): the undamped modes where sigma* = 0
+        sd = sum(float(((f[2 * c] - f[2 * c + 1]) - (prev[2 * c] - prev[2 * c + 1])).abs().pow(2).sum())
+                 for c in range(6))
+        top = [int(k) for k in dplane.argsort()[::-1][:8]]
+        print(json.dumps({"config": "diverge", "workload": "%s (%dx%dx%d)" % (args.c2_workload, st.nx, st.ny, st.nz),
+                          "iterations": done, "residual": _sig(r0, 3), "residual_next": _sig(r1, 3),
+                          "layers": {"pml_top": [0, st.L], "source_plane": st.k_s, "texture": [
+                              _sig(float(st.z_top().min()), 3), _sig(float(st.z_top().max()), 3)],
+                              "asi_end": st.z_asi_end, "glass_end": st.z_glass_end, "pml_bottom": [st.nz - st.L, st.nz]},
+                          "update_share_by_material": mat,
+                          "update_share_by_component": {names[c]: _sig(float(d2[c].sum()) / dtot, 3) for c in range(6)},
+                          "split_difference_update_vs_full": _sig(sd / dtot, 3),
+                          "top_update_planes": [[k, _sig(float(dplane[k]), 3), _sig(float(xplane[k]), 3)] for k in top],
+                          "update_share_per_8_planes": [_sig(float(dplane[i:i + 8].sum()), 2)
+                                                        for i in range(0, st.nz, 8)]}), flush=True)
+        del co, f, prev, d2, x2, eps
+        torch.cuda.empty_cache()
+
     if "c3" in which:
         stacks = batch_configs(32, seed=1)
         probs = [_stack_problem(p, torch, st, "pair", stream, dev) for st in stacks]
@@ -956,13 +1011,15 @@ def main():
                     help="complex128: binary64 adds (1) or adds and products (3) on the integer pipe "
                          "(bit-identical; thiim_set_fp64_int_ops)")
     ap.add_argument("--variant", default="", help="run one entry of the variants alone (profiling)")
-    ap.add_argument("--extended-configs", default="", help="c2,c3: convergence runs (minutes; not the headline)")
+    ap.add_argument("--extended-configs", default="",
+                    help="c2,c3,diverge: convergence runs and the growing-mode diagnosis (minutes; not the headline)")
     ap.add_argument("--c2-workload", default="stack128")
     ap.add_argument("--c2-tol-fp64", type=float, default=1e-11)
     ap.add_argument("--c2-max-fp64", type=int, default=700000)
     ap.add_argument("--c2-max-outer", type=int, default=20000)
     ap.add_argument("--c2-inner", type=int, default=50, help="complex64 iterations per FP64 defect")
     ap.add_argument("--c3-tol", type=float, default=1e-8)
+    ap.add_argument("--diverge-iters", type=int, default=200000)
     ap.add_argument("--c3-max-iters", type=int, default=24000)
     ap.add_argument("--c3-chunk", type=int, default=4000)
     ap.add_argument("--c3-max-seconds", type=float, default=1e9, help="stop C3 after this wall time")

@@ -131,14 +131,14 @@ struct Native {
 // not the differences A::sub), bit 1: the leading products); the fused
 // multiply-adds stay on the FP64 pipe.  Every operation keeps its IEEE result, and the order of
 // operations is Native<double>'s, so the results are bit-identical to it.
-// Measured on GB300 at 128^3 it is no faster: an integer addition takes ~75
-// integer instructions (twice the pipe time of the FP64 instruction it
-// replaces, in a pipe shared with the sweep's address and index work), and
-// with the additions on the integer pipe (FP64-pipe cycles down 30 %) the
-// launch takes 0.87 ms against 0.85 ms on the FP64 pipe alone; the
-// multiplications' rare-case fallback to the FP64 pipe is evaluated
-// unconditionally by the compiler, so bit 1 saves nothing.  It stays as an
-// option (off by default).
+// Measured on GB300 it does not pay: an integer addition takes ~75 integer
+// instructions (twice the pipe time of the FP64 instruction it replaces, in a
+// pipe shared with the sweep's address and index work).  With the additions
+// on the integer pipe the FP64-pipe cycles drop 28 % but the 512^3 sweep runs
+// at 3621 against 3610 MLUP/s on the FP64 pipe alone (32 x 16 tiles), and
+// with only the full-field sums there (bit 2) at 3533; the multiplications'
+// rare-case fallback to the FP64 pipe is evaluated unconditionally by the
+// compiler, so bit 1 saves nothing.  It stays as an option (off by default).
 template <int OFF>
 struct Fp64Int : Native<double> {
     static constexpr int min_blocks = 2;
