@@ -718,6 +718,39 @@ def run_extended(args):
         del co, f, prev, d2, x2, eps
         torch.cuda.empty_cache()
 
+    if "pml" in which:
+        # the same stack with other absorbing layers: cells x conductivity scale,
+        # native FP64, residual every 10k iterations
+        import dataclasses
+        base = stack_config(args.c2_workload)
+        for spec in args.pml_variants.split(","):
+            cells, scale = spec.split(":")
+            st = dataclasses.replace(base, pml_cells=int(cells))
+            st.sigma_max *= float(scale)
+            shape = (st.nz, st.ny, st.nx)
+            eps = torch.from_numpy(st.eps()).to(dev)
+            ctx = p.thiim_create(st.nx, st.ny, st.nz, p.THIIM_C128, 3, stream)
+            co = [torch.empty(shape, dtype=torch.complex128, device=dev) for _ in range(28)]
+            f = [torch.zeros(shape, dtype=torch.complex128, device=dev) for _ in range(12)]
+            traj = []
+            try:
+                with torch.cuda.stream(stream):
+                    p.thiim_build_coeffs(ctx, eps, st.sigma_pml_e(), st.sigma_pml_h(), st.omega, st.tau, st.k_s,
+                                         1.0, co)
+                p.thiim_set_coeffs(ctx, co)
+                p.thiim_set_fields(ctx, f)
+                done = 0
+                while done < args.diverge_iters:
+                    p.thiim_iterate(ctx, 10000)
+                    done += 10000
+                    traj.append([done, _sig(p.thiim_residual(ctx), 3)])
+            finally:
+                p.thiim_destroy(ctx)
+            print(json.dumps({"config": "pml", "workload": args.c2_workload, "pml_cells": st.L,
+                              "sigma_max": _sig(st.sigma_max, 3), "trajectory": traj}), flush=True)
+            del co, f, eps
+            torch.cuda.empty_cache()
+
     if "c3" in which:
         stacks = batch_configs(32, seed=1)
         probs = [_stack_problem(p, torch, st, "pair", stream, dev) for st in stacks]
@@ -1012,7 +1045,8 @@ def main():
                          "(bit-identical; thiim_set_fp64_int_ops)")
     ap.add_argument("--variant", default="", help="run one entry of the variants alone (profiling)")
     ap.add_argument("--extended-configs", default="",
-                    help="c2,c3,diverge: convergence runs and the growing-mode diagnosis (minutes; not the headline)")
+                    help="c2,c3,diverge,pml: convergence runs, the growing-mode diagnosis and absorbing-layer variants "
+                         "(minutes; not the headline)")
     ap.add_argument("--c2-workload", default="stack128")
     ap.add_argument("--c2-tol-fp64", type=float, default=1e-11)
     ap.add_argument("--c2-max-fp64", type=int, default=700000)
@@ -1020,6 +1054,7 @@ def main():
     ap.add_argument("--c2-inner", type=int, default=50, help="complex64 iterations per FP64 defect")
     ap.add_argument("--c3-tol", type=float, default=1e-8)
     ap.add_argument("--diverge-iters", type=int, default=200000)
+    ap.add_argument("--pml-variants", default="24:1,24:4,6:1", help="absorbing-layer cells:conductivity scale")
     ap.add_argument("--c3-max-iters", type=int, default=24000)
     ap.add_argument("--c3-chunk", type=int, default=4000)
     ap.add_argument("--c3-max-seconds", type=float, default=1e9, help="stop C3 after this wall time")
