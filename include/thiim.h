@@ -137,9 +137,9 @@ int thiim_set_tuning(thiim_ctx *ctx, int temporal_block, int zchunk);
  * FP64-pipe instructions at ~1.7 per SM and clock and integer instructions at
  * 64-128, so the FP64 sweep is bound by its FP64 pipe; THIIM_INT_ADD computes
  * the additions exactly in integer arithmetic instead (every operand pair,
- * without branches), THIIM_INT_MUL the leading products (normal operands and
- * results; the rest on the FP64 pipe).  The fused multiply-adds always use
- * the FP64 pipe.  Measured on GB300 the sweep is not faster with either (an
+ * without branches), THIIM_INT_SUMS only those forming the full-field sums,
+ * THIIM_INT_MUL the leading products (normal operands and results; the rest
+ * on the FP64 pipe).  The fused multiply-adds always use the FP64 pipe.  Measured on GB300 the sweep is not faster with either (an
  * integer addition costs ~75 integer instructions), so the default is 0.
  *   ops: 0 (everything on the FP64 pipe, the default), THIIM_INT_ADD,
  *        THIIM_INT_ADD | THIIM_INT_MUL, or THIIM_INT_SUMS.
