@@ -325,7 +325,7 @@ extern "C" int thiim_adjoint_iterate(thiim_ctx *c, void *const lambda[THIIM_N_FI
             s.src[i] = m == 0 ? fwd_checkpoint[i] : c->adj_states[m - 1][i];
             s.dst[i] = c->adj_states[m][i];
         }
-        if (launch_sweep_f64(s, grid, c->stream) != cudaSuccess) return THIIM_ERR_CUDA;
+        if (launch_sweep_f64_ctx(c, s, grid) != cudaSuccess) return THIIM_ERR_CUDA;
     }
     // Reverse steps n0+n_back-1 .. n0.
     AdjArgs a;

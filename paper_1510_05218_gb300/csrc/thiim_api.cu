@@ -23,8 +23,13 @@ int tile_w(const thiim_ctx *c) {
          : c->precision == THIIM_C128      ? Tile<Native<double>>::TX : Tile<Native<float>>::TX;
 }
 int tile_h(const thiim_ctx *c) {
-    return c->precision == THIIM_C128_PAIR ? Tile<PairArith<1, 1>>::TY
-         : c->precision == THIIM_C128      ? Tile<Native<double>>::TY : Tile<Native<float>>::TY;
+    if (c->precision == THIIM_C128)   // the tall FP64 tile on large grids
+        return c->n_cells >= THIIM_F64_TALL_MIN_CELLS ? Tile<Native<double>>::TY : SWEEP_TY;
+    return c->precision == THIIM_C128_PAIR ? Tile<PairArith<1, 1>>::TY : Tile<Native<float>>::TY;
+}
+
+cudaError_t launch_sweep_f64_ctx(const thiim_ctx *c, const SweepArgs &a, dim3 grid) {
+    return tile_h(c) == SWEEP_TY ? launch_sweep_f64_t8(a, grid, c->stream) : launch_sweep_f64(a, grid, c->stream);
 }
 int tiles_x(const thiim_ctx *c) { return (c->nx + tile_w(c) - 1) / tile_w(c); }
 int tiles_y(const thiim_ctx *c) { return (c->ny + tile_h(c) - 1) / tile_h(c); }
@@ -448,15 +453,15 @@ int thiim_iterate(thiim_ctx *c, int n_iters) {
         if (tbl && pair)
             e = launch_sweep_pair_tbl(a, grid, c->stream, it > 0, it < n_iters - 1);
         else if (tbl && c->precision == THIIM_C128)
-            e = launch_sweep_f64_tbl(a, grid, c->stream);
+            e = launch_sweep_f64_tbl(a, grid, c->stream, tile_h(c) != SWEEP_TY);
         else if (tbl)
             e = launch_sweep_f32_tbl(a, grid, c->stream);
         else if (pair)   // intermediate iterates stay as float4 pairs; first reads and last writes complex128
             e = launch_sweep_pair(a, grid, c->stream, it > 0, it < n_iters - 1);
         else if (c->precision == THIIM_C128 && c->fp64_int_ops)
-            e = launch_sweep_f64_int(a, grid, c->stream, (int)c->fp64_int_ops);
+            e = launch_sweep_f64_int(a, grid, c->stream, (int)c->fp64_int_ops, tile_h(c) != SWEEP_TY);
         else if (c->precision == THIIM_C128)
-            e = launch_sweep_f64(a, grid, c->stream);
+            e = launch_sweep_f64_ctx(c, a, grid);
         else if (step == 2)
             e = launch_sweep2_f32(a, grid2, c->stream);
         else

@@ -206,8 +206,10 @@ extern "C" int thiim_batch_iterate(thiim_ctx *const ctx[], int nb, int max_iters
         memcpy(d.co, pair ? c->pair_co : c->coeff, sizeof(d.co));
         d.nx = c->nx; d.ny = c->ny; d.nz = c->nz;
         d.bc = c->bc;
+        // the batch kernel's tile (compile time: Tile<A>; FP64 always on the tall tile)
+        const int bty = c->precision == THIIM_C128 ? Tile<Native<double>>::TY : tile_h(c);
         d.tiles_x = tiles_x(c);
-        d.tiles = d.tiles_x * tiles_y(c);
+        d.tiles = d.tiles_x * ((c->ny + bty - 1) / bty);
         d.zchunk = c->nz < THIIM_BATCH_ZCHUNK ? c->nz : THIIM_BATCH_ZCHUNK;   // similar item sizes across solves
         const int chunks = (c->nz + d.zchunk - 1) / d.zchunk;
         first[b] = total_items;

@@ -57,6 +57,9 @@ namespace thiim {
 bool aligned(const void *p, size_t a);
 int tiles_x(const thiim_ctx *c);
 int tiles_y(const thiim_ctx *c);
+int tile_h(const thiim_ctx *c);
+// The plain FP64 sweep on the context's FP64 tile (32 x 16 or 32 x 8, tile_h).
+cudaError_t launch_sweep_f64_ctx(const thiim_ctx *c, const SweepArgs &a, dim3 grid);
 int default_zchunk(const thiim_ctx *c);
 int ensure_partials(thiim_ctx *c, size_t ctas);
 // Sum n per-CTA partial pairs in a fixed order into out[0], out[1].

@@ -62,6 +62,14 @@ constexpr int SWEEP_PAIR_TY = THIIM_SWEEP_PAIR_TY;
 #ifndef THIIM_SWEEP_F64_TY
 #define THIIM_SWEEP_F64_TY 16
 #endif
+// Smallest grid (cells) whose FP64 sweep runs on the tall tile: below it the
+// 32 x 8 tile fills the GPU better (grid sweep: 32 x 8 faster at 64^3 ..
+// 192^3, 32 x 16 from 256^3 on).  Every FP64 sweep variant (plain, material
+// table, integer pipe) follows the same rule, so that they stay bit-identical
+// down to the per-CTA residual partials.
+#ifndef THIIM_F64_TALL_MIN_CELLS
+#define THIIM_F64_TALL_MIN_CELLS (1ull << 23)
+#endif
 template <typename A>
 struct Tile { static constexpr int TX = SWEEP_TX, TY = SWEEP_TY, MINB = A::min_blocks; };
 template <int I, int O>
@@ -80,7 +88,7 @@ cudaError_t launch_sweep_f64_t8(const SweepArgs &a, dim3 grid, cudaStream_t s);
 cudaError_t launch_sweep_f32(const SweepArgs &a, dim3 grid, cudaStream_t s);
 // The FP64 sweep with additions (offload = 1) or additions and the leading
 // products (offload = 3) on the integer pipe; bit-identical results.
-cudaError_t launch_sweep_f64_int(const SweepArgs &a, dim3 grid, cudaStream_t s, int offload);
+cudaError_t launch_sweep_f64_int(const SweepArgs &a, dim3 grid, cudaStream_t s, int offload, bool tall);
 // FP32-pair arithmetic on complex128 data: fields read as complex128
 // (in_pairs = false) or float4 pairs, written likewise; coefficients are
 // float4 pairs (see split_coeffs).
@@ -88,7 +96,7 @@ cudaError_t launch_sweep_pair(const SweepArgs &a, dim3 grid, cudaStream_t s, boo
 
 // The same sweeps reading coefficients from the (material, plane) table
 // (a.mat, a.table); pair coefficients are float4 pairs of the table.
-cudaError_t launch_sweep_f64_tbl(const SweepArgs &a, dim3 grid, cudaStream_t s);
+cudaError_t launch_sweep_f64_tbl(const SweepArgs &a, dim3 grid, cudaStream_t s, bool tall);
 cudaError_t launch_sweep_f32_tbl(const SweepArgs &a, dim3 grid, cudaStream_t s);
 cudaError_t launch_sweep_pair_tbl(const SweepArgs &a, dim3 grid, cudaStream_t s, bool in_pairs, bool out_pairs);
 

@@ -4,16 +4,22 @@
 
 namespace thiim {
 
-cudaError_t launch_sweep_f64_int(const SweepArgs &a, dim3 grid, cudaStream_t s, int offload) {
+template <int OFF>
+static void launch_int(const SweepArgs &a, dim3 grid, cudaStream_t s, bool tall) {
+    typedef Tile<Fp64Int<OFF>> T;
+    if (tall)
+        sweep_kernel<Fp64Int<OFF>, T::TX, T::TY, SWEEP_NT, T::MINB><<<grid, SWEEP_NT, 0, s>>>(a);
+    else
+        sweep_kernel<Fp64Int<OFF>, SWEEP_TX, SWEEP_TY, SWEEP_NT, T::MINB><<<grid, SWEEP_NT, 0, s>>>(a);
+}
+
+cudaError_t launch_sweep_f64_int(const SweepArgs &a, dim3 grid, cudaStream_t s, int offload, bool tall) {
     if (offload == 1)
-        sweep_kernel<Fp64Int<1>, Tile<Fp64Int<1>>::TX, Tile<Fp64Int<1>>::TY, SWEEP_NT, Tile<Fp64Int<1>>::MINB>
-            <<<grid, SWEEP_NT, 0, s>>>(a);
+        launch_int<1>(a, grid, s, tall);
     else if (offload == 3)
-        sweep_kernel<Fp64Int<3>, Tile<Fp64Int<3>>::TX, Tile<Fp64Int<3>>::TY, SWEEP_NT, Tile<Fp64Int<3>>::MINB>
-            <<<grid, SWEEP_NT, 0, s>>>(a);
+        launch_int<3>(a, grid, s, tall);
     else if (offload == 4)
-        sweep_kernel<Fp64Int<4>, Tile<Fp64Int<4>>::TX, Tile<Fp64Int<4>>::TY, SWEEP_NT, Tile<Fp64Int<4>>::MINB>
-            <<<grid, SWEEP_NT, 0, s>>>(a);
+        launch_int<4>(a, grid, s, tall);
     else
         return cudaErrorInvalidValue;
     return cudaGetLastError();

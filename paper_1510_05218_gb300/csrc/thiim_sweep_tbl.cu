@@ -4,9 +4,13 @@
 
 namespace thiim {
 
-cudaError_t launch_sweep_f64_tbl(const SweepArgs &a, dim3 grid, cudaStream_t s) {
+cudaError_t launch_sweep_f64_tbl(const SweepArgs &a, dim3 grid, cudaStream_t s, bool tall) {
     typedef Tile<Native<double>> T;
-    sweep_kernel<Native<double>, T::TX, T::TY, SWEEP_NT, T::MINB, SWEEP_PLAIN, true><<<grid, SWEEP_NT, 0, s>>>(a);
+    if (tall)
+        sweep_kernel<Native<double>, T::TX, T::TY, SWEEP_NT, T::MINB, SWEEP_PLAIN, true><<<grid, SWEEP_NT, 0, s>>>(a);
+    else
+        sweep_kernel<Native<double>, SWEEP_TX, SWEEP_TY, SWEEP_NT, SWEEP_MINB, SWEEP_PLAIN, true>
+            <<<grid, SWEEP_NT, 0, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -12,7 +12,7 @@ for the GPU kernels here:
   z planes per CTA), the shared memory one CTA needs and the data a launch
   must find again in L2; ``gpu_code_balance`` the DRAM bytes per cell and
   iteration including the halo the tiles re-read (32 x 8 cells for
-  complex64, 32 x 16 for FP64, 64 x 4 for the FP32-pair sweeps).  A candidate is
+  complex64, 32 x 16 for FP64 on large grids, 64 x 4 for the FP32-pair sweeps).  A candidate is
   admitted if its shared memory fits a CTA, its L2 set stays within half of
   L2 (the paper's "half the cache is usable for tile data" rule, Sec. III-C)
   and its grid fills the resident slots; the library default is always a
@@ -66,12 +66,18 @@ def elem_bytes(precision: int) -> int:
     return 8 if precision == 1 else 16
 
 
-def tile(precision: int):
-    """(TX, TY) of the sweep kernels a precision runs (FP64: 32 x 16)."""
-    return (PAIR_TX, PAIR_TY) if precision == 2 else ((TX, 2 * TY) if precision == 0 else (TX, TY))
+F64_TALL_MIN_CELLS = 1 << 23          # FP64 grids from here on run on 32 x 16 tiles
 
 
-def gpu_footprint(precision: int, temporal: int, zchunk: int, ctas: int, n_sm: int, l2_bytes: int):
+def tile(precision: int, cells=None):
+    """(TX, TY) of the sweep kernels a precision runs (FP64: 32 x 16 on grids of
+    at least F64_TALL_MIN_CELLS cells or when the size is not given, else 32 x 8)."""
+    if precision == 0:
+        return (TX, 2 * TY) if cells is None or cells >= F64_TALL_MIN_CELLS else (TX, TY)
+    return (PAIR_TX, PAIR_TY) if precision == 2 else (TX, TY)
+
+
+def gpu_footprint(precision: int, temporal: int, zchunk: int, ctas: int, n_sm: int, l2_bytes: int, cells=None):
     """Shared memory per CTA, resident CTAs and the L2 set that must be reused.
 
     Shared memory: the full-field sums (3 complex) of every plane the kernel
@@ -87,24 +93,24 @@ def gpu_footprint(precision: int, temporal: int, zchunk: int, ctas: int, n_sm: i
     Sec. III-C) and the grid has at least one CTA per resident slot.
     """
     b = elem_bytes(precision)
-    TX, TY = tile(precision)
+    tx, ty = tile(precision, cells)
     if temporal == 1:
-        smem = b * 3 * 2 * ((TX + 2) * (TY + 2) + (TX + 1) * (TY + 1))
-        per_sm = 5 if precision == 1 else 2
+        smem = b * 3 * 2 * ((tx + 2) * (ty + 2) + (tx + 1) * (ty + 1))
+        per_sm = 5 if precision == 1 else (3 if (precision == 0 and ty == TY) else 2)
         l2_set = 0
     else:
-        smem = b * (3 * 2 * ((TX + 4) * (TY + 4) + (TX + 3) * (TY + 3) + (TX + 2) * (TY + 2) + (TX + 1) * (TY + 1))
-                    + 6 * 2 * ((TX + 1) * (TY + 1) + TX * TY))
+        smem = b * (3 * 2 * ((tx + 4) * (ty + 4) + (tx + 3) * (ty + 3) + (tx + 2) * (ty + 2) + (tx + 1) * (ty + 1))
+                    + 6 * 2 * ((tx + 1) * (ty + 1) + tx * ty))
         per_sm = 1
     per_sm = max(1, min(per_sm, SMEM_PER_SM // max(1, smem)))
     resident = per_sm * n_sm
     if temporal != 1:
-        l2_set = min(resident, ctas) * 2 * 28 * b * (TX + 1) * (TY + 1)
+        l2_set = min(resident, ctas) * 2 * 28 * b * (tx + 1) * (ty + 1)
     return {"smem_per_cta": smem, "ctas_per_sm": per_sm, "resident_ctas": resident, "l2_set": l2_set,
             "fits": smem <= SMEM_PER_CTA and l2_set <= l2_bytes // 2 and ctas >= resident}
 
 
-def gpu_code_balance(precision: int, temporal: int, zchunk: int) -> float:
+def gpu_code_balance(precision: int, temporal: int, zchunk: int, cells=None) -> float:
     """DRAM bytes per cell and iteration if every halo cell is re-read from DRAM.
 
     One iteration reads 40 arrays (E on the (TX+2)(TY+2) region, H and the
@@ -113,7 +119,7 @@ def gpu_code_balance(precision: int, temporal: int, zchunk: int) -> float:
     read x^0 on the grown regions once and write x^2 once, per two iterations.
     """
     b = elem_bytes(precision)
-    TX, TY = tile(precision)
+    TX, TY = tile(precision, cells)
     cells = TX * TY
     z = max(1, zchunk)
     if temporal == 1:
@@ -125,14 +131,14 @@ def gpu_code_balance(precision: int, temporal: int, zchunk: int) -> float:
     return b * per_cell * (z + 3) / z
 
 
-def candidates(precision: int, nz: int, tiles: int, n_sm: int, l2_bytes: int):
+def candidates(precision: int, nz: int, tiles: int, n_sm: int, l2_bytes: int, cells=None):
     """(temporal, zchunk) pairs admitted by the footprint model, plus the default (1, 0)."""
     out = [(1, 0)]
     for temporal in ((1, 2) if precision == 1 else (1,)):
         for z in (16, 32, 64, 128, 256):
             if z > nz:
                 continue
-            fp = gpu_footprint(precision, temporal, z, tiles * math.ceil(nz / z), n_sm, l2_bytes)
+            fp = gpu_footprint(precision, temporal, z, tiles * math.ceil(nz / z), n_sm, l2_bytes, cells)
             if fp["fits"]:
                 out.append((temporal, z))
     return out
@@ -149,9 +155,9 @@ def autotune(ctx, fields, nx, ny, nz, precision, iters=20, repeats=2, stream=Non
     from . import thiim as T
 
     props = torch.cuda.get_device_properties(fields[0].device)
-    tx, ty = tile(precision)
+    tx, ty = tile(precision, nx * ny * nz)
     tiles = math.ceil(nx / tx) * math.ceil(ny / ty)
-    cands = candidates(precision, nz, tiles, props.multi_processor_count, props.L2_cache_size)
+    cands = candidates(precision, nz, tiles, props.multi_processor_count, props.L2_cache_size, nx * ny * nz)
     saved = [f.clone() for f in fields]
     times = {}
     try:

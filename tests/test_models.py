@@ -70,8 +70,11 @@ def test_footprint_model_matches_the_kernels_shared_memory():
     nvcc = build._nvcc()
     if shutil.which(nvcc) is None and not os.path.exists(nvcc):
         pytest.skip("nvcc not available")
-    cases = [("thiim_sweep_f64.cu", 0, 1, 256), ("thiim_sweep_f32.cu", 1, 1, 256),
-             ("thiim_sweep_pair_b.cu", 2, 1, 256), ("thiim_sweep2_f32.cu", 1, 2, 512)]
+    # (source, precision, iterations per launch, threads, grid cells); the
+    # FP64 sweep runs 32 x 16 tiles on large grids and 32 x 8 below 2^23 cells
+    cases = [("thiim_sweep_f64.cu", 0, 1, 256, None), ("thiim_noalloc.cu", 0, 1, 256, 64 ** 3),
+             ("thiim_sweep_f32.cu", 1, 1, 256, None), ("thiim_sweep_pair_b.cu", 2, 1, 256, None),
+             ("thiim_sweep2_f32.cu", 1, 2, 512, None)]
 
     def smem(src):
         cmd = [nvcc, *build.ARCH, "-O3", "-std=c++17", "-I", build.INCLUDE, "-I", build.CSRC, "-Xptxas", "-v",
@@ -82,7 +85,7 @@ def test_footprint_model_matches_the_kernels_shared_memory():
 
     with cf.ThreadPoolExecutor(4) as ex:
         found = list(ex.map(lambda c: smem(c[0]), cases))
-    for (src, precision, temporal, nt), sizes in zip(cases, found):
-        model = tuning.gpu_footprint(precision, temporal, 32, 8192, 152, 129 * 2 ** 20)["smem_per_cta"]
+    for (src, precision, temporal, nt, cells), sizes in zip(cases, found):
+        model = tuning.gpu_footprint(precision, temporal, 32, 8192, 152, 129 * 2 ** 20, cells)["smem_per_cta"]
         # the file's plain sweep (a second kernel there, e.g. the defect sweep, may differ)
         assert model + 2 * (nt // 32) * 8 in sizes, (src, sizes, model)

@@ -143,3 +143,48 @@ def test_noalloc_rejects_grids_beyond_its_scratch():
     assert e.value.code == -1
     torch.cuda.synchronize()
     assert not bool(torch.any(dst != 0))
+
+
+@pytest.mark.parametrize("nz", [128, 127])
+def test_fp64_tile_shape_changes_no_field_bit(nz):
+    """The FP64 sweep runs 32 x 16 tiles from 2^23 cells on (256 x 256 x 128
+    here) and 32 x 8 below it (nz = 127); thiim_step_noalloc always runs 32 x 8.
+    Each cell's arithmetic does not depend on the tile (a halo cell's H is
+    recomputed by the same operations in the same order), so the fields agree
+    bit for bit either way.  The residual sums per-CTA partials, whose grouping
+    follows the tile: equal bit for bit on the same tile, within a few
+    rounding errors (1e-13 relative) across tiles."""
+    import torch
+    import paper_1510_05218_gb300 as p
+    p.load_library()
+    nx = ny = 256
+    g = torch.Generator(device="cuda")
+    g.manual_seed(9)
+    shape = (nz, ny, nx)
+
+    def rnd(scale):
+        return torch.complex(torch.randn(shape, generator=g, device="cuda", dtype=torch.float64),
+                             torch.randn(shape, generator=g, device="cuda", dtype=torch.float64)) * scale
+
+    co = [rnd(0.3) for _ in range(28)]
+    a = [rnd(1.0) for _ in range(12)]
+    b = [torch.empty_like(t) for t in a]
+    r = p.thiim_step_noalloc(nx, ny, nz, 0, 3, a, b, co)
+    ref = [t.clone() for t in a]
+    del a
+    ctx = p.thiim_create(nx, ny, nz, 0, 3)
+    try:
+        p.thiim_set_coeffs(ctx, co)
+        p.thiim_set_fields(ctx, ref)
+        p.thiim_iterate(ctx, 1)
+        q = p.thiim_residual(ctx)
+    finally:
+        p.thiim_destroy(ctx)
+    torch.cuda.synchronize()
+    for s in range(12):
+        assert torch.equal(b[s], ref[s]), s
+    assert np.isfinite(r) and r > 0
+    if nx * ny * nz < 2 ** 23:
+        assert r == q
+    else:
+        assert abs(r - q) <= 1e-13 * q
