@@ -52,7 +52,7 @@ PRECISION_NOTE = {"c128": "with native FP64 arithmetic",
                   "pair": "with FP32-pair arithmetic (parity with the FP64 oracle <= 1e-12)",
                   "c64": "stored as complex64 with FP32 arithmetic"}
 FLOPS_PER_LUP = 248                                  # the paper's count (Sec. III-A)
-SWEEP_SRC = [os.path.join(ROOT, "paper_1510_05218_gb300", "csrc", f) for f in ("thiim_sweep.cuh", "thiim_internal.h")]
+SWEEP_SRC = [os.path.join(ROOT, "paper_1510_05218_gb300", "csrc", f) for f in ("thiim_sweep.cuh", "thiim_internal.h", "thiim_arith.cuh")]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "sweep_traffic.json")
 
 

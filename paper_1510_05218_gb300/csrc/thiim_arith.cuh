@@ -81,6 +81,8 @@ struct Native {
     static constexpr bool pairs = false;
     // resident 256-thread CTAs per SM asked of the register allocator
     static constexpr int min_blocks = sizeof(R) == 8 ? 3 : 5;
+    // how much of the next phase's once-read data the sweep prefetches into L1
+    static constexpr int l1_prefetch = sizeof(R) == 8 ? 2 : 1;
     __device__ static __forceinline__ Z zero() { Z z; z.x = R(0); z.y = R(0); return z; }
     __device__ static __forceinline__ Z ld_field(const void *b, size_t i) { return ldg_as<Z>(b, i); }
     __device__ static __forceinline__ Z ld_field_hint(const void *b, size_t i, uint64_t pol) {
@@ -241,6 +243,7 @@ struct PairArith {
     typedef zpair Z;
     static constexpr bool pairs = true;
     static constexpr int min_blocks = 2;
+    static constexpr int l1_prefetch = 2;
     __device__ static __forceinline__ Z zero() { Z z; z.x.h = z.x.l = z.y.h = z.y.l = 0.f; return z; }
     __device__ static __forceinline__ Z from_f4(float4 v) { Z z; z.x.h = v.x; z.x.l = v.y; z.y.h = v.z; z.y.l = v.w; return z; }
     __device__ static __forceinline__ Z ld_field(const void *b, size_t i) {
