@@ -89,3 +89,26 @@ def test_footprint_model_matches_the_kernels_shared_memory():
         model = tuning.gpu_footprint(precision, temporal, 32, 8192, 152, 129 * 2 ** 20, cells)["smem_per_cta"]
         # the file's plain sweep (a second kernel there, e.g. the defect sweep, may differ)
         assert model + 2 * (nt // 32) * 8 in sizes, (src, sizes, model)
+
+
+def test_fp64_tile_rule_matches_the_library():
+    """tuning.tile's FP64 size rule (32 x 16 from F64_TALL_MIN_CELLS cells on,
+    32 x 8 below) is the library's: the threshold and both tile heights are
+    read from the CUDA headers."""
+    import re
+
+    from paper_1510_05218_gb300 import build
+
+    src = open(os.path.join(build.CSRC, "thiim_internal.h")).read()
+    m = re.search(r"#define THIIM_F64_TALL_MIN_CELLS \(1ull << (\d+)\)", src)
+    assert m and tuning.F64_TALL_MIN_CELLS == 1 << int(m.group(1))
+    tall_ty = int(re.search(r"#define THIIM_SWEEP_F64_TY (\d+)", src).group(1))
+    short_ty = int(re.search(r"#define THIIM_SWEEP_TY (\d+)", src).group(1))
+    n = tuning.F64_TALL_MIN_CELLS
+    assert tuning.tile(0, n) == (tuning.TX, tall_ty)
+    assert tuning.tile(0, n - 1) == (tuning.TX, short_ty)
+    assert tuning.tile(0) == (tuning.TX, tall_ty)            # size unknown: the large-grid tile
+    assert tuning.tile(1, 64 ** 3) == tuning.tile(1) == (tuning.TX, tuning.TY)
+    # the footprint model follows: 3 CTAs/SM on the short FP64 tile, 2 on the tall one
+    assert tuning.gpu_footprint(0, 1, 32, 8192, 152, 129 * 2 ** 20, n - 1)["ctas_per_sm"] == 3
+    assert tuning.gpu_footprint(0, 1, 32, 8192, 152, 129 * 2 ** 20, n)["ctas_per_sm"] == 2
