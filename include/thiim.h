@@ -191,6 +191,10 @@ int thiim_iterate(thiim_ctx *ctx, int n_iters);
  * of every cell, accumulated in FP64.  (The split parts alone do not settle
  * where sigma* = 0: their difference is not driven, so the full fields are
  * the converging quantity.)  Returns 0 in *rel_residual when F^n = 0.
+ * The sums are formed per CTA tile and then over the tiles in a fixed order,
+ * so a result repeats bit for bit on the same grid; the FP64 sweep's tile is
+ * 32 x 16 cells on grids of at least 2^23 cells and 32 x 8 below, the same
+ * for all its variants (coefficient table, integer-pipe operations).
  * Errors: THIIM_ERR_STATE if no iteration ran since set_fields,
  * THIIM_ERR_NONFINITE if a norm is NaN or Inf, THIIM_ERR_CUDA.
  */
